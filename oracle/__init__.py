@@ -1,0 +1,192 @@
+"""FP64 CPU oracle for the ARC tracer and chemistry (ctypes binding).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the benchmark's ``cpu_baseline`` / reference leg may import this package.  It
+shares no code with the CUDA path (``paper_1807_07094_gb300``) and neither
+imports the other; both read inputs from ``workloads``.
+
+The arithmetic lives in ``arc_oracle.c`` (plain C, FP64, single thread); this
+module only compiles it with gcc, loads it and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "arc_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liborc.so")
+
+MAXG = 4
+END_SPLIT, END_ESCAPE, END_TERM = 1, 2, 3
+
+
+class OrcParams(C.Structure):
+    _fields_ = [
+        ("n", C.c_int), ("box_cm", C.c_double), ("ngroups", C.c_int),
+        ("E_group_eV", C.c_double * MAXG), ("sigma", (C.c_double * MAXG) * 3),
+        ("Y", C.c_double), ("phi", C.c_double), ("l_base", C.c_int), ("l_max", C.c_int),
+        ("term_frac", C.c_double), ("eps_sub", C.c_double), ("x_fp64", C.c_double),
+        ("isothermal", C.c_int), ("alpha_B_fixed", C.c_double), ("coll_ion", C.c_int),
+        ("z_compton", C.c_double),
+    ]
+
+
+REC_DTYPE = np.dtype([("src", "<u4"), ("level", "<i4"), ("pix", "<u8"), ("visits", "<i4"),
+                      ("end", "<i4"), ("r0", "<f8"), ("r1", "<f8"), ("geo_margin", "<f8"),
+                      ("term_margin", "<f8")], align=True)
+
+
+def build(force: bool = False) -> str:
+    """Compile liborc.so with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "arc_oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        L.orc_pix2vec_nest.argtypes = [C.c_int, C.c_uint64, dp]
+        L.orc_vec2pix_nest.argtypes = [C.c_int, dp]
+        L.orc_vec2pix_nest.restype = C.c_uint64
+        L.orc_r_split.argtypes = [C.POINTER(OrcParams), C.c_int]
+        L.orc_r_split.restype = C.c_double
+        L.orc_trace.argtypes = [C.POINTER(OrcParams), dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp,
+                                C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.orc_trace.restype = C.c_int
+        L.orc_chem.argtypes = [C.POINTER(OrcParams), C.c_int64, dp, dp, dp, dp, dp, dp, dp,
+                               C.c_double, C.POINTER(C.c_int64)]
+        L.orc_chem.restype = C.c_int
+        L.orc_rates.argtypes = [C.POINTER(OrcParams), C.c_double, dp]
+        L.orc_cooling.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, C.c_double]
+        L.orc_cooling.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def make_params(d: dict) -> OrcParams:
+    p = OrcParams()
+    p.n = int(d["n"])
+    p.box_cm = float(d["box_cm"])
+    p.ngroups = int(d["ngroups"])
+    for b in range(MAXG):
+        p.E_group_eV[b] = float(d["E_group_eV"][b]) if b < p.ngroups else 0.0
+        for s in range(3):
+            p.sigma[s][b] = float(d["sigma"][s][b]) if b < p.ngroups else 0.0
+    for k in ("Y", "phi", "term_frac", "eps_sub", "x_fp64", "alpha_B_fixed", "z_compton"):
+        setattr(p, k, float(d[k]))
+    for k in ("l_base", "l_max", "isothermal", "coll_ion"):
+        setattr(p, k, int(d[k]))
+    return p
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def pix2vec(level: int, pix: int) -> np.ndarray:
+    v = np.zeros(3)
+    lib().orc_pix2vec_nest(level, pix, _dptr(v))
+    return v
+
+
+def vec2pix(level: int, v) -> int:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return int(lib().orc_vec2pix_nest(level, _dptr(v)))
+
+
+def r_split(params: dict, level: int) -> float:
+    p = make_params(params)
+    return lib().orc_r_split(C.byref(p), level)
+
+
+def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool = False,
+          rec_cap: int = 1 << 22):
+    """One RT pass.  Returns dict(gamma[3,n,n,n], heat[3,n,n,n], budget[3],
+    nseg, nrec, recs (structured array or None))."""
+    p = make_params(params)
+    n = p.n
+    f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    nH, xHI, xHeI, xHeII = f(nH), f(xHI), f(xHeI), f(xHeII)
+    pos = f(src_pos)
+    ndot = f(src_ndot)
+    nsrc = pos.size // 3
+    gamma = np.zeros(3 * n ** 3)
+    heat = np.zeros(3 * n ** 3)
+    budget = np.zeros(3)
+    nrec = C.c_int64(0)
+    nseg = C.c_int64(0)
+    recs = np.zeros(rec_cap if records else 0, dtype=REC_DTYPE)
+    rc = lib().orc_trace(C.byref(p), _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII), nsrc,
+                         _dptr(pos), _dptr(ndot), _dptr(gamma), _dptr(heat), _dptr(budget),
+                         recs.ctypes.data if records else None, rec_cap if records else 0,
+                         C.byref(nrec), C.byref(nseg))
+    if rc == -2:
+        raise RuntimeError(f"oracle record buffer too small: {nrec.value} > {rec_cap}")
+    if rc != 0:
+        raise ValueError(f"orc_trace failed ({rc})")
+    return dict(gamma=gamma.reshape(3, n, n, n), heat=heat.reshape(3, n, n, n), budget=budget,
+                nseg=int(nseg.value), nrec=int(nrec.value),
+                recs=recs[: nrec.value] if records else None)
+
+
+def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float):
+    """Chemistry over dt; returns (xHI, xHeI, xHeII, T, nsub, capped) as float64."""
+    p = make_params(params)
+    f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1)).copy()
+    nH = f(nH)
+    xHI, xHeI, xHeII, T = f(xHI), f(xHeI), f(xHeII), f(T)
+    g = f(gamma)
+    h = f(heat)
+    ncell = nH.size
+    assert g.size == 3 * ncell and h.size == 3 * ncell
+    nsub = C.c_int64(0)
+    capped = lib().orc_chem(C.byref(p), ncell, _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII),
+                            _dptr(T), _dptr(g), _dptr(h), float(dt), C.byref(nsub))
+    return xHI, xHeI, xHeII, T, int(nsub.value), int(capped)
+
+
+def rates(params: dict, T: float) -> np.ndarray:
+    p = make_params(params)
+    out = np.zeros(6)
+    lib().orc_rates(C.byref(p), float(T), _dptr(out))
+    return out
+
+
+def cooling(params: dict, T, nH, nHI, nHeI, nHeII, ne) -> float:
+    p = make_params(params)
+    return float(lib().orc_cooling(C.byref(p), T, nH, nHI, nHeI, nHeII, ne))
+
+
+def run(params: dict, w, nsteps: int, trace_every: int = 1):
+    """Free-running oracle: trace + chemistry per step.  Returns final fields."""
+    xHI, xHeI, xHeII, T = (np.asarray(a, np.float64).reshape(-1).copy()
+                           for a in (w.xHI, w.xHeI, w.xHeII, w.T))
+    hist = []
+    for k in range(nsteps):
+        tr = trace(params, w.nH, xHI, xHeI, xHeII, w.src_pos, w.src_ndot)
+        xHI, xHeI, xHeII, T, nsub, capped = chem(params, w.nH, xHI, xHeI, xHeII, T,
+                                                 tr["gamma"], tr["heat"], w.dt_s)
+        hist.append(dict(budget=tr["budget"], nseg=tr["nseg"], nsub=nsub))
+    n = w.n
+    sh = (n, n, n)
+    return xHI.reshape(sh), xHeI.reshape(sh), xHeII.reshape(sh), T.reshape(sh), hist

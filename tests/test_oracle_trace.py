@@ -1,0 +1,230 @@
+"""Pins of the oracle's ray tracer (Sec. 2.1, 2.4, Eq. ion) against closed forms.
+
+* exit distances and escaped photons in a uniform medium (ray-box slab
+  intersection, N_out = N_in exp(-tau)), including the ray tree of leaves;
+* per-ray cell-visit counts = 1 + number of grid planes crossed (closed form);
+* rays per cell face at the split radius equal phi;
+* optically thin shells: Gamma(r) -> Ndot sigma / (4 pi r^2);
+* global photon conservation: emitted = absorbed + escaped to 1e-9, and
+  sum_cells Gamma n V = absorbed;
+* N co-located sources of luminosity L/N reproduce one source of L (Sec. 4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def uniform_params(n, kappa_cell, Y=0.0, phi=4.0, l_max=14, G=1):
+    """One group, pure H, sigma chosen so that a cell of n_H=1, x=1 has optical
+    depth kappa_cell per cell length."""
+    box = n * 1.0e20
+    sig = np.zeros((3, G))
+    sig[0, :] = kappa_cell / 1.0e20
+    return dict(n=n, box_cm=box, ngroups=G, E_group_eV=[13.6] * G, sigma=sig.tolist(), Y=Y,
+                phi=phi, l_base=1, l_max=l_max, term_frac=1e-6, eps_sub=0.1, x_fp64=1e-4,
+                isothermal=1, alpha_B_fixed=2.59e-13, coll_ion=0, z_compton=-1.0)
+
+
+def fields(n, nH=1.0, x=1.0):
+    f = lambda v: np.full((n, n, n), v)
+    return f(nH), f(x), f(0.0), f(0.0)
+
+
+def exit_distance(o, u, n):
+    """Distance along u from o (inside [0,n)^3) to the box surface (slab method)."""
+    t = np.inf
+    for a in range(3):
+        if u[a] > 0:
+            t = min(t, (n - o[a]) / u[a])
+        elif u[a] < 0:
+            t = min(t, (0 - o[a]) / u[a])
+    return t
+
+
+def expected_leaves(p, o, n):
+    """Leaves of the ray tree in a transparent box, built independently:
+    a level-l ray starting at r0 escapes if its exit distance is below r_split(l)."""
+    leaves = []
+
+    def walk(l, pix, r0):
+        u = oracle.pix2vec(l, pix)
+        x = o + r0 * u
+        if np.any(np.floor(x) < 0) or np.any(np.floor(x) >= n):
+            leaves.append((l, pix, r0))
+            return
+        rs = oracle.r_split(p, l) if l < p["l_max"] else np.inf
+        d = exit_distance(o, u, n)
+        if d <= rs:
+            leaves.append((l, pix, d))
+        else:
+            for k in range(4):
+                walk(l + 1, 4 * pix + k, rs)
+
+    for q in range(48):
+        walk(1, q, 0.0)
+    return leaves
+
+
+@pytest.mark.parametrize("o", [(8.5, 8.5, 8.5), (3.25, 10.5, 7.75), (0.5, 0.5, 0.5)])
+def test_uniform_medium_escape_closed_form(o):
+    n = 16
+    kap = 0.02
+    p = uniform_params(n, kap)
+    o = np.array(o)
+    ndot = 1e50
+    r = oracle.trace(p, *fields(n), o[None, :], np.array([[ndot]]), records=True)
+    recs = r["recs"]
+    esc = recs[recs["end"] == oracle.END_ESCAPE]
+    leaves = expected_leaves(p, o, n)
+    got = sorted((int(a["level"]), int(a["pix"])) for a in esc)
+    assert got == sorted((l, q) for l, q, _ in leaves)
+    dist = {(l, q): d for l, q, d in leaves}
+    esc_expect = 0.0
+    for a in esc:
+        d = dist[(int(a["level"]), int(a["pix"]))]
+        assert abs(a["r1"] - d) < 1e-9 * max(1, d)
+        n0 = ndot / 48 / 4 ** (a["level"] - 1)
+        esc_expect += n0 * math.exp(-kap * d)
+    em, ab, es = r["budget"]
+    assert abs(es - esc_expect) < 1e-12 * em
+    assert abs(em - ab - es) < 1e-9 * em
+
+
+def planes_crossed(o, u, r0, r1):
+    x0 = o + r0 * u
+    x1 = o + r1 * u
+    return int(np.abs(np.floor(x1) - np.floor(x0)).sum())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_visit_counts_closed_form(seed):
+    """visits = 1 + grid planes crossed between the ray's start and end."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = 12
+    p = uniform_params(n, 0.0)
+    nH = rng.uniform(0.1, 2.0, (n, n, n))
+    p["sigma"][0][0] = 0.3 / 1e20
+    o = W.quantise_pos(rng.uniform(2, 10, 3))
+    r = oracle.trace(p, nH, np.ones_like(nH), np.zeros_like(nH), np.zeros_like(nH),
+                     o[None, :], np.array([[1e50]]), records=True)
+    recs = r["recs"]
+    assert len(recs) > 100
+    checked = 0
+    for a in recs:
+        if a["geo_margin"] < 1e-9 or a["visits"] == 0:
+            continue
+        u = oracle.pix2vec(int(a["level"]), int(a["pix"]))
+        r1 = a["r1"] - (1e-9 if a["end"] == oracle.END_ESCAPE else 0.0)
+        assert a["visits"] == 1 + planes_crossed(o, u, a["r0"], r1), a
+        checked += 1
+    assert checked > 0.9 * len(recs)
+
+
+def test_rays_per_face_at_split_equals_phi():
+    """At the split radius the level-l rays alive cover the sphere with exactly
+    phi rays per unit cell face: 12 4^l / (4 pi r_split(l)^2) = phi."""
+    for phi in (1.0, 3.0, 4.0):
+        p = uniform_params(64, 0.0, phi=phi)
+        n = 64
+        o = np.array([32.0, 32.0, 32.0]) + W.quantise_pos([0.1, 0.2, 0.3])
+        r = oracle.trace(p, *fields(n, 0.0), o[None, :], np.array([[1e50]]), records=True)
+        recs = r["recs"]
+        for l in range(1, 5):
+            m = (recs["level"] == l) & (recs["end"] == oracle.END_SPLIT)
+            assert m.sum() == 12 * 4 ** l, (phi, l, m.sum())
+            rs = recs["r1"][m]
+            assert np.allclose(rs, rs[0])
+            assert abs(12 * 4 ** l / (4 * math.pi * rs[0] ** 2) - phi) < 1e-12 * phi
+        # levels grow with distance: a ray at distance r has level min{l: r < r_split(l)}
+        for a in recs:
+            l = int(a["level"])
+            assert a["r1"] <= oracle.r_split(p, l) + 1e-12
+            if l > 1:
+                assert a["r0"] >= oracle.r_split(p, l - 1) - 1e-12
+
+
+def test_optically_thin_shells():
+    """Thin medium: shell-averaged Gamma(r) = Ndot sigma / (4 pi r^2) (Eq. ion in
+    the small-tau limit, the same expression the paper uses for its optically
+    thin region, Sec. 2.6)."""
+    n = 48
+    sig = 6.3e-18
+    box = n * 1e21
+    p = uniform_params(n, 0.0)
+    p["box_cm"] = box
+    p["sigma"][0][0] = sig
+    nH = np.full((n, n, n), 1e-3)
+    x = np.full((n, n, n), 1e-8)
+    o = np.array([24.0, 24.0, 24.0]) + 1 / 4096
+    ndot = 1e50
+    r = oracle.trace(p, nH, x, np.zeros_like(x), np.zeros_like(x), o[None, :], np.array([[ndot]]))
+    g = r["gamma"][0]
+    c = np.indices((n, n, n)).reshape(3, -1).T + 0.5
+    rad = np.sqrt(((c - o) ** 2).sum(1))
+    dx = box / n
+    for r0 in (6, 9, 12, 16, 20):
+        m = (rad >= r0) & (rad < r0 + 2)
+        # weight each cell by its radius^2 to remove the within-shell 1/r^2 slope
+        est = (g.ravel()[m] * (rad[m] * dx) ** 2).mean() * 4 * math.pi / (ndot * sig)
+        assert abs(est - 1.0) < 0.02, (r0, est)
+
+
+def test_budget_and_cell_sum_identity():
+    w = W.thermal_128(n=32, box_kpc=6.6 / 4)
+    # partly ionised, lumpy gas so that all three species absorb
+    rng = np.random.Generator(np.random.PCG64(3))
+    xHI = rng.uniform(0.0, 1.0, w.xHI.shape)
+    xHeI = rng.uniform(0.0, 1.0, w.xHI.shape)
+    xHeII = (1 - xHeI) * rng.uniform(0, 1, w.xHI.shape)
+    nH = w.nH * rng.lognormal(0, 1, w.xHI.shape)
+    src = W.quantise_pos(np.array([[16.3, 11.1, 20.7], [3.5, 3.5, 3.5]]))
+    ndot = np.array([w.src_ndot[0], 3 * w.src_ndot[0]])
+    p = w.params()
+    r = oracle.trace(p, nH, xHI, xHeI, xHeII, src, ndot)
+    em, ab, es = r["budget"]
+    assert abs(em - ndot.sum()) < 1e-12 * em
+    assert abs(em - ab - es) < 1e-9 * em
+    y = w.Y / (4 * (1 - w.Y))
+    dx = w.box_cm / w.n
+    ns = np.stack([nH * xHI, y * nH * xHeI, y * nH * xHeII])
+    # photons absorbed per second in the cells, from the per-absorber rates
+    cell_sum = (r["gamma"] * ns).sum() * dx ** 3
+    assert abs(cell_sum - ab) < 1e-9 * ab
+
+
+def test_source_scaling_invariance():
+    """N co-located sources of luminosity L/N give the result of one source of L (Sec. 4)."""
+    w = W.thermal_128(n=24, box_kpc=6.6 * 24 / 128)
+    p = w.params()
+    o = W.quantise_pos([[7.3, 12.6, 9.1]])
+    L = w.src_ndot[0] * 40
+    r1 = oracle.trace(p, w.nH, w.xHI, w.xHeI, w.xHeII, o, L[None, :])
+    r10 = oracle.trace(p, w.nH, w.xHI, w.xHeI, w.xHeII, np.repeat(o, 10, 0),
+                       np.repeat(L[None, :] / 10, 10, 0))
+    g1, g10 = r1["gamma"], r10["gamma"]
+    m = g1 > 1e-6 * g1.max()
+    assert np.max(np.abs(g10[m] / g1[m] - 1)) < 1e-12
+    assert np.allclose(r10["budget"], r1["budget"], rtol=1e-12)
+
+
+def test_termination_threshold_and_residual():
+    """Rays stop once their photons fall below term_frac of their share of the
+    emission; the residual stays in the grid, so the budget still closes."""
+    n = 16
+    p = uniform_params(n, 13.4)          # the stromgren_32 neutral-cell optical depth
+    o = np.array([8.5, 8.5, 8.5])
+    r = oracle.trace(p, *fields(n), o[None, :], np.array([[1e48]]), records=True)
+    recs = r["recs"]
+    term = recs[recs["end"] == oracle.END_TERM]
+    assert (recs["end"] != oracle.END_ESCAPE).all()
+    # level-1 rays keep exp(-13.4 * 0.977) = 2e-6 of their photons at the split
+    # radius, so they split; their children fall below 1e-6 within ~1 cell
+    assert len(term) == 192 and (term["level"] == 2).all()
+    assert term["r1"].max() < 3.0
+    assert (term["term_margin"] > 0).all()
+    em, ab, es = r["budget"]
+    assert es == 0.0 and abs(em - ab) < 1e-12 * em
