@@ -1,0 +1,223 @@
+/*
+ * arc.h -- C ABI of libarc, a single-GPU (sm_103a) implementation of the hot
+ * path of ARC, the photon-conserving adaptive ray tracer of Hartley & Ricotti
+ * (arXiv 1807.07094): per-source HEALPix ray tracing with photon-conserving
+ * multi-frequency absorption, and the per-cell H/He ionisation and thermal
+ * update that consumes its rates.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units      CGS.  Positions are in grid units: cell (i,j,k) spans
+ *            [i,i+1) x [j,j+1) x [k,k+1); coordinate x maps to index i.
+ * Layout     Every per-cell array is FP32, C order [i][j][k] (k fastest),
+ *            n^3 elements; per-species arrays are species-major
+ *            [s][i][j][k] with s = 0 HI, 1 HeI, 2 HeII.
+ * Ownership  The context owns every device buffer it allocates; inputs are
+ *            copied in.  Pointers returned by arc_trace stay valid until the
+ *            next arc_trace or arc_destroy.
+ * Streams    All work is queued on the stream given to arc_create (NULL = the
+ *            legacy default stream).  Only the calls documented as
+ *            synchronising wait for the GPU.
+ * Errors     Every call returns an arc_status.  Errors found by a kernel
+ *            (queue overflow, a bounded wait that gave up, a chemistry cell
+ *            that hit the sub-step cap) are recorded in a device status word
+ *            and returned by the next synchronising call.  arc_last_error()
+ *            gives a one-line text for the most recent failure.
+ * Threads    A context must not be used by two host threads at once.
+ */
+#ifndef ARC_H
+#define ARC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ARC_MAX_GROUPS 4    /* frequency groups carried per ray */
+#define ARC_MAX_LEVEL 15    /* deepest HEALPix level a ray may reach */
+
+typedef enum {
+    ARC_OK = 0,
+    ARC_E_INVALID = 1,   /* bad argument or input field value                       */
+    ARC_E_OOM = 2,       /* device allocation failed                                */
+    ARC_E_CUDA = 3,      /* a CUDA runtime call failed                              */
+    ARC_E_TIMEOUT = 4,   /* a bounded wait in the persistent tracer gave up         */
+    ARC_E_BUDGET = 5,    /* photon budget failed to close within 1e-9               */
+    ARC_E_STATE = 6,     /* call out of order (e.g. trace before fields are set)    */
+    ARC_E_OVERFLOW = 7,  /* ray work queue or record buffer capacity exceeded       */
+    ARC_E_SUBSTEP = 8    /* a chemistry cell hit the sub-step cap                   */
+} arc_status;
+
+typedef struct arc_ctx arc_ctx;
+
+/* Uniform cubic grid of n^3 cells and physical side box_cm (Sec. 2.3). */
+typedef struct {
+    int n;               /* cells per side, 1 .. 4096                              */
+    double box_cm;       /* side length [cm]                                        */
+} arc_grid;
+
+/*
+ * Method parameters.  Frequency groups (Sec. 2.2): each group b is one
+ * frequency with photon energy E_group_eV[b] and cross sections sigma[s][b]
+ * [cm^2] for s = HI, HeI, HeII.  The defaults used by the workloads are in
+ * the comments.
+ */
+typedef struct {
+    int ngroups;                          /* 1 .. ARC_MAX_GROUPS                        */
+    double E_group_eV[ARC_MAX_GROUPS];    /* mean photon energy per group [eV]          */
+    double sigma[3][ARC_MAX_GROUPS];      /* sigma_{s,b} [cm^2]                         */
+    double Y;                             /* helium mass fraction (0.24; 0 = pure H)    */
+    double phi;                           /* split when fewer than phi rays cross a
+                                             cell face (4)  -- Sec. 2.4, Fig. 1         */
+    int l_base;                           /* HEALPix level of emitted packets (1)       */
+    int l_max;                            /* deepest level; l_max rays never split (14) */
+    double term_frac;                     /* terminate a ray below this fraction of its
+                                             share of the emission (1e-6)              */
+    double eps_sub;                       /* sub-cycle fractional-change limit (0.1)
+                                             -- Sec. 2.7                               */
+    double x_fp64;                        /* cells with x_HI below this take their
+                                             species update in FP64 (1e-4); also the
+                                             floor of the step limiter                 */
+    int isothermal;                       /* 1: temperature fixed                      */
+    double alpha_B_fixed;                 /* > 0: constant case-B alpha_HII [cm^3/s]   */
+    int coll_ion;                         /* 1: collisional ionisation on              */
+    double z_compton;                     /* >= 0: Compton cooling off the CMB at z    */
+} arc_params;
+
+/* Counters of the last arc_trace / arc_chem_update (arc_stats synchronises). */
+typedef struct {
+    uint64_t segments;       /* ray-cell segments traced                              */
+    uint64_t rays;           /* rays traced (every node of every ray tree)            */
+    uint64_t splits;         /* rays that split into four children                    */
+    uint64_t terminated;     /* rays stopped by the photon threshold                  */
+    uint64_t escaped_rays;   /* rays that left the box                                */
+    uint64_t donations;      /* work items moved to the global queue                  */
+    uint32_t max_level;      /* deepest HEALPix level reached                         */
+    uint32_t error_word;     /* raw device status bits of the last trace/chemistry    */
+    uint64_t chem_substeps;  /* sub-steps summed over cells                           */
+    uint64_t chem_fp64_substeps; /* sub-steps taken on the FP64 branch                */
+    uint64_t chem_capped;    /* cells that hit the sub-step cap                       */
+    double trace_ms;         /* device time of the last trace (events)                */
+    double chem_ms;          /* device time of the last chemistry update              */
+    uint64_t segments_total; /* segments summed over every trace of this context      */
+    uint64_t traces_total;   /* traces run by this context                            */
+} arc_stats_t;
+
+/* One record per ray (test aid, see arc_set_records). */
+typedef struct {
+    uint32_t src;            /* source index in the order sources were added           */
+    uint8_t level;           /* HEALPix level                                          */
+    uint8_t end;             /* 1 split, 2 escaped, 3 terminated                       */
+    uint16_t pad;
+    uint64_t pix;            /* nested pixel index at that level                       */
+    uint32_t visits;         /* cell segments traced, zero-length ones included       */
+    float r1;                /* distance from the source where the ray ended [cells]  */
+} arc_ray_rec;
+
+/*
+ * arc_create -- allocate a context for an n^3 grid (Sec. 2.3).
+ *   out      receives the context (set to NULL on failure)
+ *   g, p     grid and parameters, copied
+ *   stream   cudaStream_t to queue all work on (NULL = legacy default stream)
+ * Allocates the field, rate, accumulator and work-queue buffers on the
+ * current device.  Returns ARC_E_INVALID for out-of-range parameters,
+ * ARC_E_OOM if an allocation fails.
+ */
+arc_status arc_create(arc_ctx** out, const arc_grid* g, const arc_params* p, void* stream);
+
+/*
+ * arc_set_fields -- copy in the gas state (Sec. 2.3): hydrogen number density
+ * nH [cm^-3], neutral fractions x_HI = n_HI/n_H, x_HeI = n_HeI/n_He, singly
+ * ionised fraction x_HeII = n_HeII/n_He (n_He = Y/(4(1-Y)) n_H), temperature
+ * T [K].  n^3 FP32 each, C order; on_device = 1 for device pointers, 0 for
+ * host pointers.  Validates: finite values, nH >= 0, fractions in [0,1],
+ * x_HeI + x_HeII <= 1, T > 0; returns ARC_E_INVALID otherwise (the context's
+ * fields are then unspecified).  Synchronises.
+ */
+arc_status arc_set_fields(arc_ctx* ctx, const float* nH, const float* xHI, const float* xHeI,
+                          const float* xHeII, const float* T, int on_device);
+
+/*
+ * arc_add_sources -- append point sources (Sec. 2.1, 2.4).
+ *   pos   nsrc*3 host doubles, grid units, inside [0,n)^3
+ *   ndot  nsrc*ngroups host doubles, photons/s emitted in each group
+ * Each source emits 12*4^l_base rays sharing its output equally (Sec. 2.4).
+ * Positions are rounded to FP32 on the device; sources with no emission are
+ * kept but trace no rays.  Returns ARC_E_INVALID for a position outside the
+ * box or a negative/NaN rate.
+ */
+arc_status arc_add_sources(arc_ctx* ctx, int nsrc, const double* pos, const double* ndot);
+
+/* arc_clear_sources -- remove all sources. */
+arc_status arc_clear_sources(arc_ctx* ctx);
+
+/*
+ * arc_trace -- one radiative-transfer pass over all sources (Sec. 2.1 steps
+ * i and iii; Sec. 2.4 Eq. ion; Sec. 2.8 photoheating).
+ *   dt      time step [s]; only scales the photon counts in budget
+ *   gamma   receives a device pointer to 3*n^3 photoionisation rates per
+ *           absorber [1/s] (species-major, C order); may be NULL
+ *   heat    receives a device pointer to 3*n^3 photoheating rates per
+ *           absorber [erg/s]; may be NULL
+ *   budget  NULL, or host double[4] receiving photons over dt:
+ *           [0] launched into rays, [1] absorbed in cells, [2] escaped from
+ *           the box, [3] emitted by the sources (FP64 input sum).  [0] differs
+ *           from [3] only by the FP32 rounding of each ray's initial share.
+ * With budget != NULL the call synchronises and returns ARC_E_BUDGET if
+ * |launched - absorbed - escaped| > 1e-9 launched, ARC_E_TIMEOUT or
+ * ARC_E_OVERFLOW if the tracer recorded such an error.
+ */
+arc_status arc_trace(arc_ctx* ctx, double dt, float** gamma, float** heat, double* budget);
+
+/*
+ * arc_chem_update -- advance the gas state by dt [s] with the rates of the
+ * last arc_trace held constant (Sec. 2.7 Eqs. diffeq and anninos, sub-cycled;
+ * Sec. 2.8 heating and cooling).  Asynchronous.  Cells whose x_HI is below
+ * x_fp64 take their species update in FP64.
+ */
+arc_status arc_chem_update(arc_ctx* ctx, double dt);
+
+/*
+ * arc_step -- arc_trace followed by arc_chem_update, replayed from a CUDA
+ * graph captured on the first call (and re-captured when dt or the sources
+ * change).  Asynchronous.
+ */
+arc_status arc_step(arc_ctx* ctx, double dt);
+
+/*
+ * arc_get_fields -- copy out x_HI, x_HeI, x_HeII, T (n^3 FP32 each, C order)
+ * to device (on_device = 1) or host memory; any pointer may be NULL.
+ * Synchronises.
+ */
+arc_status arc_get_fields(arc_ctx* ctx, float* xHI, float* xHeI, float* xHeII, float* T,
+                          int on_device);
+
+/*
+ * arc_set_records -- test aid: when buf (device memory of cap arc_ray_rec)
+ * is not NULL, the next traces write one record per ray; the count is
+ * returned by arc_get_record_count.  Records cost a global atomic per ray.
+ */
+arc_status arc_set_records(arc_ctx* ctx, void* buf, int64_t cap);
+arc_status arc_get_record_count(arc_ctx* ctx, int64_t* count);
+
+/* arc_stats -- counters of the last trace and chemistry update.  Synchronises. */
+arc_status arc_stats(arc_ctx* ctx, arc_stats_t* out);
+
+/*
+ * arc_set_tuning -- launch shape of the persistent tracer: threads per block
+ * (multiple of 32, 64..1024), blocks per SM (0 = occupancy limit) and local
+ * work-stack entries per warp (power of two, 16..256).  0 keeps a value.
+ */
+arc_status arc_set_tuning(arc_ctx* ctx, int block_threads, int blocks_per_sm, int stack_entries);
+
+/* Text of the most recent error on this context (never NULL). */
+const char* arc_last_error(const arc_ctx* ctx);
+
+/* Release every buffer of the context.  NULL is ignored. */
+void arc_destroy(arc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

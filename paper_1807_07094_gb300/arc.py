@@ -1,0 +1,322 @@
+"""Thin Python binding of libarc (include/arc.h).
+
+Argument marshalling only: every step of the tracer and the chemistry runs in
+the CUDA kernels of libarc.so.  There is no CPU fallback: if the library is
+missing or fails to load, every call raises.  PyTorch is used only to hold
+device memory and to name the CUDA stream.
+
+Functions keep the C names (arc_create, arc_set_fields, arc_add_sources,
+arc_trace, arc_chem_update, arc_step, arc_get_fields, arc_stats, ...).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MAX_GROUPS = 4
+MAX_LEVEL = 15
+
+ARC_OK, ARC_E_INVALID, ARC_E_OOM, ARC_E_CUDA, ARC_E_TIMEOUT, ARC_E_BUDGET, ARC_E_STATE, \
+    ARC_E_OVERFLOW, ARC_E_SUBSTEP = range(9)
+STATUS_NAMES = ["ARC_OK", "ARC_E_INVALID", "ARC_E_OOM", "ARC_E_CUDA", "ARC_E_TIMEOUT",
+                "ARC_E_BUDGET", "ARC_E_STATE", "ARC_E_OVERFLOW", "ARC_E_SUBSTEP"]
+END_SPLIT, END_ESCAPE, END_TERM = 1, 2, 3
+
+
+class ArcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class ArcGrid(C.Structure):
+    _fields_ = [("n", C.c_int), ("box_cm", C.c_double)]
+
+
+class ArcParams(C.Structure):
+    _fields_ = [
+        ("ngroups", C.c_int), ("E_group_eV", C.c_double * MAX_GROUPS),
+        ("sigma", (C.c_double * MAX_GROUPS) * 3), ("Y", C.c_double), ("phi", C.c_double),
+        ("l_base", C.c_int), ("l_max", C.c_int), ("term_frac", C.c_double),
+        ("eps_sub", C.c_double), ("x_fp64", C.c_double), ("isothermal", C.c_int),
+        ("alpha_B_fixed", C.c_double), ("coll_ion", C.c_int), ("z_compton", C.c_double),
+    ]
+
+
+class ArcStats(C.Structure):
+    _fields_ = [
+        ("segments", C.c_uint64), ("rays", C.c_uint64), ("splits", C.c_uint64),
+        ("terminated", C.c_uint64), ("escaped_rays", C.c_uint64), ("donations", C.c_uint64),
+        ("max_level", C.c_uint32), ("error_word", C.c_uint32), ("chem_substeps", C.c_uint64),
+        ("chem_fp64_substeps", C.c_uint64), ("chem_capped", C.c_uint64),
+        ("trace_ms", C.c_double), ("chem_ms", C.c_double), ("segments_total", C.c_uint64),
+        ("traces_total", C.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REC_DTYPE = np.dtype([("src", "<u4"), ("level", "u1"), ("end", "u1"), ("pad", "<u2"),
+                      ("pix", "<u8"), ("visits", "<u4"), ("r1", "<f4")], align=True)
+assert REC_DTYPE.itemsize == 24
+
+_lib = None
+
+# every exported entry point of include/arc.h with its ctypes signature
+_SIGS = {
+    "arc_create": ([C.POINTER(C.c_void_p), C.POINTER(ArcGrid), C.POINTER(ArcParams), C.c_void_p], C.c_int),
+    "arc_set_fields": ([C.c_void_p] + [C.c_void_p] * 5 + [C.c_int], C.c_int),
+    "arc_add_sources": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "arc_clear_sources": ([C.c_void_p], C.c_int),
+    "arc_trace": ([C.c_void_p, C.c_double, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                   C.POINTER(C.c_double)], C.c_int),
+    "arc_chem_update": ([C.c_void_p, C.c_double], C.c_int),
+    "arc_step": ([C.c_void_p, C.c_double], C.c_int),
+    "arc_get_fields": ([C.c_void_p] + [C.c_void_p] * 4 + [C.c_int], C.c_int),
+    "arc_set_records": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
+    "arc_get_record_count": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "arc_stats": ([C.c_void_p, C.POINTER(ArcStats)], C.c_int),
+    "arc_set_tuning": ([C.c_void_p, C.c_int, C.c_int, C.c_int], C.c_int),
+    "arc_last_error": ([C.c_void_p], C.c_char_p),
+    "arc_destroy": ([C.c_void_p], None),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libarc.so (building it first if asked).  Raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"libarc is not built ({path}); run paper_1807_07094_gb300.build")
+            _build.build()
+        L = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != ARC_OK:
+        msg = load().arc_last_error(ctx).decode() if ctx else "arc_create failed"
+        raise ArcError(status, msg)
+
+
+def make_params(d: dict) -> ArcParams:
+    p = ArcParams()
+    p.ngroups = int(d["ngroups"])
+    for b in range(MAX_GROUPS):
+        p.E_group_eV[b] = float(d["E_group_eV"][b]) if b < p.ngroups else 0.0
+        for s in range(3):
+            p.sigma[s][b] = float(d["sigma"][s][b]) if b < p.ngroups else 0.0
+    for k in ("Y", "phi", "term_frac", "eps_sub", "x_fp64", "alpha_B_fixed", "z_compton"):
+        setattr(p, k, float(d[k]))
+    for k in ("l_base", "l_max", "isothermal", "coll_ion"):
+        setattr(p, k, int(d[k]))
+    return p
+
+
+def _ptr_and_kind(a):
+    """(address, on_device) of a float32 contiguous torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise ValueError("fields must be contiguous float32")
+            return a.data_ptr(), 1 if a.is_cuda else 0
+    except ImportError:
+        pass
+    a = np.asarray(a)
+    if a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise ValueError("fields must be contiguous float32")
+    return a.ctypes.data, 0
+
+
+def current_stream_handle() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class _DevView:
+    """__cuda_array_interface__ over a device pointer owned by the context."""
+
+    def __init__(self, ptr: int, shape, typestr="<f4"):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, dtype="float32"):
+    """Zero-copy torch view of a context-owned device buffer."""
+    import torch
+    ts = {"float32": "<f4"}[dtype]
+    return torch.as_tensor(_DevView(ptr, shape, ts), device="cuda")
+
+
+# ----------------------------------------------------------------- C names
+def arc_create(grid: ArcGrid, params: ArcParams, stream: Optional[int] = None) -> int:
+    L = load()
+    h = C.c_void_p()
+    st = L.arc_create(C.byref(h), C.byref(grid), C.byref(params), C.c_void_p(stream or 0))
+    _check(None, st)
+    return h.value
+
+
+def arc_destroy(ctx: int) -> None:
+    load().arc_destroy(C.c_void_p(ctx))
+
+
+def arc_set_fields(ctx, nH, xHI, xHeI, xHeII, T) -> None:
+    ptrs = [_ptr_and_kind(a) for a in (nH, xHI, xHeI, xHeII, T)]
+    kinds = {k for _, k in ptrs}
+    if len(kinds) != 1:
+        raise ValueError("fields must all be host or all be device arrays")
+    _check(ctx, load().arc_set_fields(C.c_void_p(ctx), *[C.c_void_p(p) for p, _ in ptrs], kinds.pop()))
+
+
+def arc_add_sources(ctx, pos, ndot) -> None:
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    ndot = np.ascontiguousarray(ndot, dtype=np.float64)
+    _check(ctx, load().arc_add_sources(C.c_void_p(ctx), pos.shape[0], pos.ctypes.data, ndot.ctypes.data))
+
+
+def arc_clear_sources(ctx) -> None:
+    _check(ctx, load().arc_clear_sources(C.c_void_p(ctx)))
+
+
+def arc_trace(ctx, dt: float, budget: bool = True):
+    """Returns (gamma_ptr, heat_ptr, budget[4] or None)."""
+    g = C.c_void_p()
+    h = C.c_void_p()
+    b = (C.c_double * 4)() if budget else None
+    _check(ctx, load().arc_trace(C.c_void_p(ctx), float(dt), C.byref(g), C.byref(h), b))
+    return g.value, h.value, (np.array(list(b)) if budget else None)
+
+
+def arc_chem_update(ctx, dt: float) -> None:
+    _check(ctx, load().arc_chem_update(C.c_void_p(ctx), float(dt)))
+
+
+def arc_step(ctx, dt: float) -> None:
+    _check(ctx, load().arc_step(C.c_void_p(ctx), float(dt)))
+
+
+def arc_get_fields(ctx, xHI=None, xHeI=None, xHeII=None, T=None) -> None:
+    outs = [xHI, xHeI, xHeII, T]
+    kinds = set()
+    ptrs = []
+    for o in outs:
+        if o is None:
+            ptrs.append(None)
+            continue
+        p, k = _ptr_and_kind(o)
+        kinds.add(k)
+        ptrs.append(p)
+    if len(kinds) > 1:
+        raise ValueError("outputs must all be host or all be device arrays")
+    _check(ctx, load().arc_get_fields(C.c_void_p(ctx), *[C.c_void_p(p) if p else None for p in ptrs],
+                                      kinds.pop() if kinds else 0))
+
+
+def arc_set_records(ctx, buf_ptr: int, cap: int) -> None:
+    _check(ctx, load().arc_set_records(C.c_void_p(ctx), C.c_void_p(buf_ptr or 0), int(cap)))
+
+
+def arc_get_record_count(ctx) -> int:
+    n = C.c_int64()
+    _check(ctx, load().arc_get_record_count(C.c_void_p(ctx), C.byref(n)))
+    return int(n.value)
+
+
+def arc_stats(ctx) -> dict:
+    s = ArcStats()
+    _check(ctx, load().arc_stats(C.c_void_p(ctx), C.byref(s)))
+    return s.as_dict()
+
+
+def arc_set_tuning(ctx, block_threads=0, blocks_per_sm=0, stack_entries=0) -> None:
+    _check(ctx, load().arc_set_tuning(C.c_void_p(ctx), int(block_threads), int(blocks_per_sm),
+                                      int(stack_entries)))
+
+
+def arc_last_error(ctx) -> str:
+    return load().arc_last_error(C.c_void_p(ctx)).decode()
+
+
+# ----------------------------------------------------------------- convenience
+class Arc:
+    """Context owner: ``with Arc(n, box_cm, params_dict) as a: ...``."""
+
+    def __init__(self, n: int, box_cm: float, params: dict, stream: Optional[int] = None):
+        self.n = int(n)
+        g = ArcGrid(self.n, float(box_cm))
+        self.ctx = arc_create(g, make_params(params), stream)
+
+    def close(self):
+        if self.ctx:
+            arc_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, nH, xHI, xHeI, xHeII, T):
+        arc_set_fields(self.ctx, nH, xHI, xHeI, xHeII, T)
+
+    def add_sources(self, pos, ndot):
+        arc_add_sources(self.ctx, pos, ndot)
+
+    def clear_sources(self):
+        arc_clear_sources(self.ctx)
+
+    def trace(self, dt: float = 1.0, budget: bool = True):
+        """Returns (gamma, heat) as zero-copy torch views [3,n,n,n] and the budget."""
+        g, h, b = arc_trace(self.ctx, dt, budget)
+        sh = (3, self.n, self.n, self.n)
+        return device_view(g, sh), device_view(h, sh), b
+
+    def chem(self, dt: float):
+        arc_chem_update(self.ctx, dt)
+
+    def step(self, dt: float):
+        arc_step(self.ctx, dt)
+
+    def get_fields(self):
+        n3 = (self.n,) * 3
+        out = [np.empty(n3, np.float32) for _ in range(4)]
+        arc_get_fields(self.ctx, *out)
+        return out
+
+    def stats(self) -> dict:
+        return arc_stats(self.ctx)
+
+    def set_records(self, buf, cap: int):
+        arc_set_records(self.ctx, buf, cap)
+
+    def record_count(self) -> int:
+        return arc_get_record_count(self.ctx)
+
+    def set_tuning(self, block_threads=0, blocks_per_sm=0, stack_entries=0):
+        arc_set_tuning(self.ctx, block_threads, blocks_per_sm, stack_entries)

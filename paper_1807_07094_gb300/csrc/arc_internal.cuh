@@ -1,0 +1,177 @@
+// arc_internal.cuh -- device-side data layout and helpers shared by the libarc
+// translation units (tracer, chemistry, host API).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "arc.h"
+
+namespace arc {
+
+// ---------------------------------------------------------------------------
+// Units.  Photon rates on the device are carried in units of PHOT_UNIT
+// photons/s so that rays of sources from 1e30 to 1e55 photons/s stay inside
+// the normal FP32 range at every HEALPix level (a level-15 ray of a 1e47
+// source carries ~8e-4 units, one of a 1e51 source at level 1 ~2e9 units).
+// ---------------------------------------------------------------------------
+constexpr double PHOT_UNIT = 1e40;
+constexpr double EV_ERG = 1.602176634e-12;
+constexpr double K_BOLTZ = 1.380649e-16;
+
+// Status bits of the device status word.
+enum : uint32_t {
+    ERR_TIMEOUT = 1u << 0,    // an idle warp waited past its bound
+    ERR_QUEUE_FULL = 1u << 1, // the global work queue could not take an entry
+    ERR_RECORDS = 1u << 2,    // the ray record buffer overflowed
+    ERR_SUBSTEP = 1u << 3,    // a chemistry cell hit the sub-step cap
+    ERR_CAS_SPIN = 1u << 4,   // a queue CAS loop exceeded its bound
+    ERR_FIELDS = 1u << 5,     // invalid gas field value found on the device
+};
+
+// ---------------------------------------------------------------------------
+// Internal cell layout: 8x8x8 bricks, bricks in C order over ceil(n/8)^3,
+// cells inside a brick in Morton order (k bit first).  A ray crossing a brick
+// touches a handful of 128-byte lines instead of one line per cell as in the
+// C-order layout, which raises L2 reuse of the absorber and accumulator
+// records.  User-facing arrays stay in C order; the prep and finalize passes
+// convert.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    // three bits b2 b1 b0 -> b2 0 0 b1 0 0 b0
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
+}
+__host__ __device__ __forceinline__ uint64_t brick_index(int i, int j, int k, int nb) {
+    const uint64_t b = ((uint64_t)(i >> 3) * nb + (uint64_t)(j >> 3)) * nb + (uint64_t)(k >> 3);
+    const uint32_t m = spread3((uint32_t)k & 7u) | (spread3((uint32_t)j & 7u) << 1) |
+                       (spread3((uint32_t)i & 7u) << 2);
+    return (b << 9) | m;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint32_t m) {
+    return (m & 1u) | ((m >> 2) & 2u) | ((m >> 4) & 4u);
+}
+
+// ---------------------------------------------------------------------------
+// Ray work item: the not-yet-traced children k_next..3 of one split (or the
+// 4 pixels pixbase..pixbase+3 of an emitted group).  32 bytes, one sector.
+// key bits: 0..47 pixbase (4 x parent pixel), 48..55 level, 56..58 k_next.
+// ---------------------------------------------------------------------------
+struct __align__(16) Entry {
+    uint64_t key;
+    uint32_t src;
+    float r;        // start radius of the children [cells]
+    float4 N;       // photons per child per group [PHOT_UNIT]
+};
+static_assert(sizeof(Entry) == 32, "entry is one 32-byte sector");
+
+__host__ __device__ __forceinline__ uint64_t make_key(uint64_t pixbase, int level, int k) {
+    return pixbase | ((uint64_t)level << 48) | ((uint64_t)k << 56);
+}
+__host__ __device__ __forceinline__ uint64_t key_pixbase(uint64_t key) { return key & 0xFFFFFFFFFFFFull; }
+__host__ __device__ __forceinline__ int key_level(uint64_t key) { return (int)((key >> 48) & 0xFF); }
+__host__ __device__ __forceinline__ int key_k(uint64_t key) { return (int)((key >> 56) & 0x7); }
+
+// Per-source record on the device (sources sorted by luminosity, brightest first).
+struct __align__(16) SourceDev {
+    float4 pos_thr;   // x, y, z [cells], photon threshold of one l_base ray [PHOT_UNIT]
+    float4 N0;        // photons of one l_base ray per group [PHOT_UNIT]
+    uint32_t id;      // index in the order the caller added the sources
+    uint32_t pad[3];
+};
+
+// Arguments of the tracer kernels.
+struct TraceArgs {
+    int n, nb, ng, l_base, l_max;
+    const float4* kappa;      // [brick cells] optical depth per cell length, per group
+    float4* acc;              // [2*brick cells] photons absorbed per group: hi, lo pairs
+    const SourceDev* src;
+    int nsrc;
+    float rsplit[ARC_MAX_LEVEL + 1];   // split distance per level [cells]
+    // emitted work: static array consumed by ticket
+    const Entry* seeds;
+    int nseeds;
+    unsigned int* seed_head;
+    // dynamic work queue (bounded MPMC ring, per-slot sequence numbers)
+    Entry* qdata;
+    unsigned long long* qseq;
+    unsigned long long* qhead;
+    unsigned long long* qtail;
+    unsigned long long qmask;
+    // bookkeeping
+    long long* live;          // rays not yet finished (approximate until quiescence)
+    int* n_idle;              // warps waiting for work
+    unsigned int* status;     // device status word (ERR_*)
+    unsigned int* heartbeat;  // progress counter for the idle-wait bound
+    double* escaped;          // photons that left the box [PHOT_UNIT]
+    unsigned long long* counters;  // segments, rays, splits, terminated, escaped, donations, maxlevel
+    arc_ray_rec* recs;
+    unsigned long long* nrec;
+    unsigned long long rec_cap;
+    int stack_log2;           // local work stack entries per warp = 1 << stack_log2
+    unsigned long long idle_timeout_ns;
+};
+
+enum { CNT_SEG = 0, CNT_RAYS, CNT_SPLIT, CNT_TERM, CNT_ESC, CNT_DONATE, CNT_MAXLEVEL, CNT_N };
+// counters[CNT_N] and [CNT_N + 1] (segments and traces over the context's life)
+// follow the per-trace counters and are never reset
+enum { CNT_SEG_TOTAL = CNT_N, CNT_TRACES_TOTAL, CNT_ALL };
+
+// Launch wrappers (defined in arc_trace.cu / arc_chem.cu).
+struct PrepArgs {
+    int n, nb, ng;
+    const float* nH;
+    const float* xHI;
+    const float* xHeI;
+    const float* xHeII;
+    float y;                  // n_He / n_H
+    float sig_dx[3][ARC_MAX_GROUPS];   // sigma_{s,b} * dx [cm^3]: kappa = sum_s sig_dx n_s
+    float4* kappa;
+    float4* acc;
+};
+struct FinalizeArgs {
+    int n, nb, ng;
+    const float* nH;
+    const float* xHI;
+    const float* xHeI;
+    const float* xHeII;
+    float y;
+    float sig[3][ARC_MAX_GROUPS];      // sigma_{s,b} [cm^2]
+    float egap_erg[3][ARC_MAX_GROUPS]; // (E_b - E_s) [erg]
+    float scale;              // PHOT_UNIT / V [1/(s cm^3)]
+    const float4* acc;
+    float* gamma;             // 3*n^3
+    float* heat;              // 3*n^3
+    double* absorbed_part;    // per block FP64 partial of absorbed photons [PHOT_UNIT]
+};
+struct ChemArgs {
+    long long ncell;
+    float* nH;
+    float* xHI;
+    float* xHeI;
+    float* xHeII;
+    float* T;
+    const float* gamma;
+    const float* heat;
+    double dt;
+    float y, eps, xfloor, alpha_fixed, tcmb, compton_coef;
+    int isothermal, coll_ion, compton;
+    unsigned int* status;
+    unsigned long long* counters;  // substeps, fp64 substeps, capped
+};
+
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s);
+cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_budget(const double* part, int nparts, const double* escaped, double* out,
+                          cudaStream_t s);
+cudaError_t launch_validate(const float* nH, const float* xHI, const float* xHeI,
+                            const float* xHeII, const float* T, long long ncell,
+                            unsigned int* status, cudaStream_t s);
+cudaError_t launch_make_seeds(const SourceDev* src, int nsrc, int l_base, Entry* seeds,
+                              cudaStream_t s);
+cudaError_t launch_chem(const ChemArgs& a, cudaStream_t s);
+int trace_smem_bytes(int block, int stack_log2);
+const void* trace_kernel_ptr();
+
+}  // namespace arc

@@ -1,0 +1,802 @@
+// arc_trace.cu -- ray-tracing kernels of libarc (sm_103a).
+//
+//   k_prep       absorber optical depth per cell length, accumulators zeroed
+//                (Sec. 2.1 step i; absorber densities from Sec. 2.3)
+//   k_make_seeds 12 4^l_base / 4 work items per source (Sec. 2.1 step iii.a)
+//   k_reset      work queue and counters
+//   k_trace      persistent tracer: HEALPix pix2vec, cell-by-cell traversal,
+//                Eq. (ion) absorption, split into 4 children, termination
+//                (Sec. 2.1 step iii, Sec. 2.4)
+//   k_finalize   per-group absorbed photons -> per-absorber photoionisation
+//                and photoheating rates (Eq. ion, Sec. 2.8), FP64 partial sums
+//                of the absorbed photons
+//   k_budget     FP64 photon budget
+//
+// Design (GPU-first; differs from the paper's one-ray-per-core level loop):
+// * one lane = one ray; a warp keeps the pending children of its splits on a
+//   small deque in shared memory and always takes the newest (depth first), so
+//   memory stays bounded by the tree depth instead of 48 4^l rays per level;
+// * all sources run in one persistent launch: emitted work items are taken by
+//   ticket from a static array ordered brightest first, and busy warps donate
+//   the oldest (largest) pending subtrees to a bounded lock-free ring when
+//   other warps are idle;
+// * per segment a ray reads one 16-byte record of optical depth per cell
+//   length (one per group) and adds the photons absorbed per group into the
+//   cell with one vector atomic; the species split of Eq. (ion) depends only
+//   on the cell's absorber densities, so it is applied once per cell in
+//   k_finalize instead of per segment;
+// * photon conservation is exact by construction: each segment moves exactly
+//   D = N_before - N_after from the ray into the cell (Sterbenz-exact FP32
+//   subtraction) and the cell sums are compensated (TwoSum on the value the
+//   atomic returns, error added to a second word).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "arc_internal.cuh"
+
+namespace arc {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long ld_relaxed_s(const long long* p) {
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// 128-bit atomic add returning the previous value (sm_90+ vector atomics)
+__device__ __forceinline__ float4 atom_add_v4(float4* a, float4 v) {
+    float4 o;
+    asm volatile("atom.global.add.v4.f32 {%0,%1,%2,%3}, [%4], {%5,%6,%7,%8};"
+                 : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+                 : "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+    return o;
+}
+__device__ __forceinline__ void red_add_v4(float4* a, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(a), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ float4 ldg_f4(const float4* p) { return __ldg(p); }
+
+// rounding error of a + b (Knuth TwoSum, round-to-nearest throughout)
+__device__ __forceinline__ float two_sum_err(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Eq. (ion) for one group: the fraction 1 - exp(-tau) of the ray's photons
+// is absorbed.  Returns the deposit D and updates N so that D + N_new equals
+// N_old exactly: whichever of the two is the larger is formed first and the
+// other as a Sterbenz-exact difference.
+__device__ __forceinline__ float absorb(float& N, float tau) {
+    const float a = -expm1f(-tau);
+    const float A = __fmul_rn(N, a);
+    const float Nn = __fsub_rn(N, A);        // exact when a >= 1/2 (A in [N/2, N])
+    const float D = a >= 0.5f ? A : __fsub_rn(N, Nn);   // exact when a < 1/2 (Nn in [N/2, N])
+    N = Nn;
+    return D;
+}
+
+// compensated vector deposit into a cell's (hi, lo) accumulator pair
+__device__ __forceinline__ void deposit(float4* acc, uint64_t idx, float4 v) {
+    float4* hi = acc + 2 * idx;
+    const float4 old = atom_add_v4(hi, v);
+    float4 e;
+    e.x = two_sum_err(old.x, v.x);
+    e.y = two_sum_err(old.y, v.y);
+    e.z = two_sum_err(old.z, v.z);
+    e.w = two_sum_err(old.w, v.w);
+    if (e.x != 0.f || e.y != 0.f || e.z != 0.f || e.w != 0.f) red_add_v4(hi + 1, e);
+}
+
+// ------------------------------------------------------------------ HEALPix
+__device__ __forceinline__ uint32_t even_bits(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+
+// Centre of nested pixel pix at level (nside = 2^level) as a unit vector.
+// The 12 base faces form three rows of four (north, equator, south); inside a
+// face the pixel's (x, y) come from the even/odd bits of its index, which fix
+// its ring (latitude) and its position along the ring (longitude).
+__device__ float3 healpix_dir(int level, uint64_t pix) {
+    const int ns = 1 << level;
+    const uint32_t face = (uint32_t)(pix >> (2 * level));
+    const uint32_t ipf = (uint32_t)(pix & ((1ull << (2 * level)) - 1ull));
+    const int ix = (int)even_bits(ipf), iy = (int)even_bits(ipf >> 1);
+    const int row = (int)(face >> 2);
+    const int ring = (row + 2) * ns - ix - iy - 1;      // 1 .. 4 ns - 1 from the north pole
+    int nr, shift;
+    float z, sth;
+    if (ring < ns || ring > 3 * ns) {                   // polar caps: z = +-(1 - nr^2 / (3 ns^2))
+        nr = ring < ns ? ring : 4 * ns - ring;
+        const float f = (float)nr / (float)ns;
+        const float a = f * f * (1.0f / 3.0f);
+        z = ring < ns ? 1.0f - a : a - 1.0f;
+        sth = sqrtf(a * (2.0f - a));
+        shift = 0;
+    } else {                                            // belt: z linear in the ring index
+        nr = ns;
+        z = (float)(2 * ns - ring) * (2.0f / 3.0f) / (float)ns;
+        sth = sqrtf((1.0f - z) * (1.0f + z));
+        shift = (ring - ns) & 1;
+    }
+    const int lon = 2 * (int)(face & 3u) + (row == 1 ? 0 : 1);
+    int jp = (lon * nr + ix - iy + 1 + shift) >> 1;     // numerator is always even
+    if (jp > 4 * ns) jp -= 4 * ns;
+    if (jp < 1) jp += 4 * ns;
+    const float q = (float)(2 * jp - shift - 1) / (float)(4 * nr);   // longitude / pi
+    float sp, cp;
+    sincospif(q, &sp, &cp);
+    return make_float3(sth * cp, sth * sp, z);
+}
+
+// ------------------------------------------------------------------ work queue
+// Bounded multi-producer multi-consumer ring (one sequence word per slot): a
+// slot at position p is free for the producer when seq == p and holds data for
+// the consumer when seq == p + 1.  Both sides only retry a CAS; nothing waits
+// on another thread, so the operations are lock-free.
+__device__ bool q_push(const TraceArgs& A, const Entry& e) {
+    unsigned long long pos = ld_relaxed(A.qtail);
+    for (int it = 0; it < (1 << 20); ++it) {
+        unsigned long long* seq = &A.qseq[pos & A.qmask];
+        const unsigned long long s = ld_acquire(seq);
+        const long long dif = (long long)(s - pos);
+        if (dif == 0) {
+            if (atomicCAS(A.qtail, pos, pos + 1) == pos) {
+                Entry* d = &A.qdata[pos & A.qmask];
+                __stcg(reinterpret_cast<float4*>(d), *reinterpret_cast<const float4*>(&e));
+                __stcg(reinterpret_cast<float4*>(d) + 1, e.N);
+                st_release(seq, pos + 1);
+                return true;
+            }
+            pos = ld_relaxed(A.qtail);
+        } else if (dif < 0) {
+            return false;   // full
+        } else {
+            pos = ld_relaxed(A.qtail);
+        }
+    }
+    atomicOr(A.status, ERR_CAS_SPIN);
+    return false;
+}
+
+__device__ bool q_pop(const TraceArgs& A, Entry& e) {
+    unsigned long long pos = ld_relaxed(A.qhead);
+    for (int it = 0; it < (1 << 20); ++it) {
+        unsigned long long* seq = &A.qseq[pos & A.qmask];
+        const unsigned long long s = ld_acquire(seq);
+        const long long dif = (long long)(s - (pos + 1));
+        if (dif == 0) {
+            if (atomicCAS(A.qhead, pos, pos + 1) == pos) {
+                const Entry* d = &A.qdata[pos & A.qmask];
+                const float4 a = __ldcg(reinterpret_cast<const float4*>(d));
+                const float4 b = __ldcg(reinterpret_cast<const float4*>(d) + 1);
+                *reinterpret_cast<float4*>(&e) = a;
+                e.N = b;
+                st_release(seq, pos + A.qmask + 1);
+                return true;
+            }
+            pos = ld_relaxed(A.qhead);
+        } else if (dif < 0) {
+            return false;   // empty (or the producer has not published yet)
+        } else {
+            pos = ld_relaxed(A.qhead);
+        }
+    }
+    atomicOr(A.status, ERR_CAS_SPIN);
+    return false;
+}
+
+// ------------------------------------------------------------------ ray state
+enum : int { EV_NONE = 0, EV_SPLIT = 1, EV_ESC = 2, EV_TERM = 3 };
+
+struct Ray {
+    float ox, oy, oz;      // source position [cells]
+    float ix, iy, iz;      // 1/u per axis (+-inf for u = 0)
+    float tx, ty, tz;      // distance to the next plane per axis
+    int cx, cy, cz;        // current cell
+    float r, rstop, thr;
+    float4 N;
+    uint64_t pix;
+    uint32_t src;
+    int level;
+    uint32_t visits;
+};
+
+__device__ __forceinline__ float next_plane_t(int c, float o, float inv) {
+    // u > 0 (inv > 0): plane c + 1;  u < 0: plane c
+    return ((float)(c + (inv > 0.0f ? 1 : 0)) - o) * inv;
+}
+
+// Start child k of entry e in this lane.  Returns EV_ESC if the child starts
+// outside the box (it then carries its photons straight to the escape ledger).
+__device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int k, Ray& R) {
+    R.level = key_level(e.key);
+    R.pix = key_pixbase(e.key) + (uint64_t)k;
+    R.src = e.src;
+    R.r = e.r;
+    R.N = e.N;
+    R.visits = 0;
+    const SourceDev* S = &A.src[e.src];
+    const float4 pt = __ldg(&S->pos_thr);
+    R.ox = pt.x;
+    R.oy = pt.y;
+    R.oz = pt.z;
+    R.thr = ldexpf(pt.w, -2 * (R.level - A.l_base));
+    R.rstop = (R.level < A.l_max) ? A.rsplit[R.level] : INFINITY;
+    const float3 u = healpix_dir(R.level, R.pix);
+    R.ix = 1.0f / u.x;   // +-inf when the component is zero
+    R.iy = 1.0f / u.y;
+    R.iz = 1.0f / u.z;
+    R.cx = (int)floorf(fmaf(R.r, u.x, R.ox));
+    R.cy = (int)floorf(fmaf(R.r, u.y, R.oy));
+    R.cz = (int)floorf(fmaf(R.r, u.z, R.oz));
+    const int n = A.n;
+    if (R.cx < 0 || R.cx >= n || R.cy < 0 || R.cy >= n || R.cz < 0 || R.cz >= n) return EV_ESC;
+    R.tx = (u.x != 0.0f) ? next_plane_t(R.cx, R.ox, R.ix) : INFINITY;
+    R.ty = (u.y != 0.0f) ? next_plane_t(R.cy, R.oy, R.iy) : INFINITY;
+    R.tz = (u.z != 0.0f) ? next_plane_t(R.cz, R.oz, R.iz) : INFINITY;
+    return EV_NONE;
+}
+
+// One cell segment (Sec. 2.4): to the nearest X/Y/Z boundary or the split
+// distance, Eq. (ion) absorption in every group, deposit, then step.
+__device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
+    const float t = fminf(R.tx, fminf(R.ty, R.tz));
+    const bool split = R.rstop <= t;
+    const float r1 = split ? R.rstop : t;
+    const float ds = fmaxf(r1 - R.r, 0.0f);
+    const uint64_t idx = brick_index(R.cx, R.cy, R.cz, A.nb);
+    const float4 kap = ldg_f4(&A.kappa[idx]);
+    const float4 N0 = R.N;
+    float4 D;
+    D.x = absorb(R.N.x, kap.x * ds);
+    D.y = absorb(R.N.y, kap.y * ds);
+    D.z = absorb(R.N.z, kap.z * ds);
+    D.w = absorb(R.N.w, kap.w * ds);
+    const float sumN = R.N.x + R.N.y + R.N.z + R.N.w;
+    const bool term = sumN < R.thr;
+    if (term) {
+        // below threshold: every remaining photon stays in this cell
+        D = N0;
+        R.N = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (D.x > 0.f || D.y > 0.f || D.z > 0.f || D.w > 0.f) deposit(A.acc, idx, D);
+    R.visits++;
+    R.r = r1;
+    if (term) return EV_TERM;
+    if (split) return EV_SPLIT;
+    // step across the nearest face; ties go to the lowest axis (x, y, z)
+    const int n = A.n;
+    if (R.tx <= R.ty && R.tx <= R.tz) {
+        R.cx += (R.ix > 0.f) ? 1 : -1;
+        if (R.cx < 0 || R.cx >= n) return EV_ESC;
+        R.tx = next_plane_t(R.cx, R.ox, R.ix);
+    } else if (R.ty <= R.tz) {
+        R.cy += (R.iy > 0.f) ? 1 : -1;
+        if (R.cy < 0 || R.cy >= n) return EV_ESC;
+        R.ty = next_plane_t(R.cy, R.oy, R.iy);
+    } else {
+        R.cz += (R.iz > 0.f) ? 1 : -1;
+        if (R.cz < 0 || R.cz >= n) return EV_ESC;
+        R.tz = next_plane_t(R.cz, R.oz, R.iz);
+    }
+    return EV_NONE;
+}
+
+constexpr int SEG_BATCH = 4;          // segments per lane between warp event rounds
+constexpr int HEARTBEAT_EVERY = 1024; // event rounds between progress signals
+
+__global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int cap = 1 << A.stack_log2;
+    const unsigned cmask = (unsigned)cap - 1u;
+    Entry* stack = reinterpret_cast<Entry*>(smem_raw) + (size_t)wib * cap;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    // deque [bot, top) of pending work items, indices modulo cap (warp-uniform)
+    unsigned bot = 0, top = 0;
+    long long live_delta = 0;          // lane 0 only: rays created minus finished, not yet flushed
+    unsigned long long nseg = 0, nrays = 0, nsplit = 0, nterm = 0, nesc = 0, ndon = 0;
+    unsigned maxlev = 0;
+    double esc_photons = 0.0;
+    unsigned round = 0;
+
+    Ray R;
+    bool active = false;
+    int ev = EV_NONE;
+
+    auto flush_live = [&]() {
+        if (lane == 0 && live_delta != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(A.live), (unsigned long long)live_delta);
+            live_delta = 0;
+        }
+    };
+    // move the oldest `cnt` local items to the global queue (all lanes call)
+    auto donate = [&](unsigned cnt) {
+        flush_live();   // rays made visible to other warps must be counted first
+        __syncwarp();
+        while (cnt > 0) {
+            const unsigned chunk = cnt < 32u ? cnt : 32u;
+            if ((unsigned)lane < chunk) {
+                const Entry e = stack[(bot + lane) & cmask];
+                if (!q_push(A, e)) atomicOr(A.status, ERR_QUEUE_FULL);
+            }
+            __syncwarp();
+            bot += chunk;
+            ndon += chunk;
+            cnt -= chunk;
+        }
+    };
+
+    bool done = false;
+    while (!done) {
+        // ---------------------------------------------------------------- refill
+        unsigned idle = __ballot_sync(FULL, !active);
+        if (idle) {
+            if (top == bot && (idle == FULL || (__popc(idle) >= 16 && (round & 3) == 0))) {
+                // local deque empty: fetch from the emitted items, then the ring
+                const bool all_idle = (idle == FULL);
+                int got = 0;   // items placed on the deque (warp-uniform)
+                int wanted = (__popc(idle) + 3) >> 2;
+                if (lane == 0) {
+                    unsigned t0 = 0;
+                    if (ld_relaxed_u32(A.seed_head) < (unsigned)A.nseeds) {
+                        t0 = atomicAdd(A.seed_head, (unsigned)wanted);
+                        int avail = A.nseeds - (int)t0;
+                        got = avail < 0 ? 0 : (avail < wanted ? avail : wanted);
+                    }
+                    if (got == 0) {
+                        Entry e;
+                        if (q_pop(A, e)) {
+                            stack[top & cmask] = e;
+                            got = -1;
+                        }
+                    } else {
+                        for (int i = 0; i < got; ++i) stack[(top + i) & cmask] = A.seeds[t0 + i];
+                    }
+                }
+                got = __shfl_sync(FULL, got, 0);
+                __syncwarp();
+                if (got < 0) {
+                    top += 1;
+                } else if (got > 0) {
+                    top += (unsigned)got;
+                } else if (all_idle) {
+                    // nothing anywhere for now: wait (bounded) for donations or the end
+                    flush_live();
+                    int result = 0;   // 1 = got work, 2 = finished, 3 = gave up
+                    if (lane == 0) {
+                        atomicAdd(A.n_idle, 1);
+                        unsigned long long t_last = now_ns();
+                        unsigned hb_last = ld_relaxed_u32(A.heartbeat);
+                        long long live_last = ld_relaxed_s(A.live);
+                        unsigned sleep = 32;
+                        // bounded: 10 s (idle_timeout_ns) or 2^24 polls without any
+                        // sign of progress elsewhere ends the wait with an error
+                        for (unsigned poll = 0; poll < (1u << 24); ++poll) {
+                            Entry e;
+                            if (q_pop(A, e)) {
+                                stack[top & cmask] = e;
+                                result = 1;
+                                break;
+                            }
+                            const long long lv = ld_relaxed_s(A.live);
+                            if (lv == 0) {
+                                result = 2;
+                                break;
+                            }
+                            if (ld_relaxed_u32(A.status) & (ERR_TIMEOUT | ERR_CAS_SPIN)) {
+                                result = 3;
+                                break;
+                            }
+                            const unsigned hb = ld_relaxed_u32(A.heartbeat);
+                            const unsigned long long tn = now_ns();
+                            if (hb != hb_last || lv != live_last) {
+                                hb_last = hb;
+                                live_last = lv;
+                                t_last = tn;
+                                poll = 0;
+                            } else if (tn - t_last > A.idle_timeout_ns) {
+                                atomicOr(A.status, ERR_TIMEOUT);
+                                result = 3;
+                                break;
+                            }
+                            __nanosleep(sleep);
+                            if (sleep < 2048) sleep <<= 1;
+                        }
+                        if (result == 0) {
+                            atomicOr(A.status, ERR_TIMEOUT);
+                            result = 3;
+                        }
+                        atomicSub(A.n_idle, 1);
+                    }
+                    result = __shfl_sync(FULL, result, 0);
+                    __syncwarp();
+                    if (result == 1) {
+                        top += 1;
+                    } else {
+                        done = true;
+                        break;
+                    }
+                }
+            }
+            // hand the children of the newest items to idle lanes (depth first)
+            while (idle != 0 && top != bot) {
+                const Entry e = stack[(top - 1) & cmask];
+                const int k0 = key_k(e.key);
+                const int avail = 4 - k0;
+                const int rank = __popc(idle & lt_mask);
+                const bool mine = ((idle >> lane) & 1u) && rank < avail;
+                const unsigned taken = __ballot_sync(FULL, mine);
+                if (mine) {
+                    ev = start_ray(A, e, k0 + rank, R);
+                    active = true;
+                    nrays++;
+                    maxlev = max(maxlev, (unsigned)R.level);
+                }
+                idle &= ~taken;
+                __syncwarp();
+                const int ntake = __popc(taken);
+                if (ntake >= avail) {
+                    top -= 1;
+                } else if (lane == 0) {
+                    stack[(top - 1) & cmask].key = make_key(key_pixbase(e.key), key_level(e.key), k0 + ntake);
+                }
+                __syncwarp();
+            }
+        }
+
+        // ------------------------------------------------------------ trace
+        if (active && ev == EV_NONE) {
+#pragma unroll 1
+            for (int it = 0; it < SEG_BATCH; ++it) {
+                ev = segment(A, R);
+                nseg++;
+                if (ev != EV_NONE) break;
+            }
+        }
+
+        // ------------------------------------------------------------ events
+        const bool has_ev = active && ev != EV_NONE;
+        const unsigned evm = __ballot_sync(FULL, has_ev);
+        if (evm) {
+            // per-ray records (test aid)
+            if (A.recs != nullptr) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.nrec, (unsigned long long)__popc(evm));
+                base = __shfl_sync(FULL, base, 0);
+                if (has_ev) {
+                    const unsigned long long slot = base + __popc(evm & lt_mask);
+                    if (slot < A.rec_cap) {
+                        arc_ray_rec q;
+                        q.src = A.src[R.src].id;
+                        q.level = (uint8_t)R.level;
+                        q.end = (uint8_t)ev;
+                        q.pad = 0;
+                        q.pix = R.pix;
+                        q.visits = R.visits;
+                        q.r1 = R.r;
+                        A.recs[slot] = q;
+                    } else {
+                        atomicOr(A.status, ERR_RECORDS);
+                    }
+                }
+            }
+            const bool is_split = has_ev && ev == EV_SPLIT;
+            const bool is_end = has_ev && ev != EV_SPLIT;
+            if (is_end) {
+                if (ev == EV_ESC) {
+                    esc_photons += (double)R.N.x + (double)R.N.y + (double)R.N.z + (double)R.N.w;
+                    nesc++;
+                } else {
+                    nterm++;
+                }
+                active = false;
+                ev = EV_NONE;
+            }
+            const unsigned sm = __ballot_sync(FULL, is_split);
+            const unsigned em = evm & ~sm;
+            if (lane == 0) live_delta += 3 * (long long)__popc(sm) - (long long)__popc(em);
+            if (sm) {
+                // make room: donate the oldest items if the deque would overflow
+                const unsigned need = (unsigned)__popc(sm);
+                const unsigned size = top - bot;
+                if (size + need > (unsigned)cap) donate(size + need - (unsigned)cap / 2u);
+                if (is_split) {
+                    // children 1..3 wait on the deque; this lane continues with child 0
+                    Entry e;
+                    e.key = make_key(R.pix << 2, R.level + 1, 1);
+                    e.src = R.src;
+                    e.r = R.r;
+                    e.N = make_float4(R.N.x * 0.25f, R.N.y * 0.25f, R.N.z * 0.25f, R.N.w * 0.25f);
+                    stack[(top + __popc(sm & lt_mask)) & cmask] = e;
+                    nsplit++;
+                    ev = start_ray(A, e, 0, R);
+                    nrays++;
+                    maxlev = max(maxlev, (unsigned)R.level);
+                }
+                __syncwarp();
+                top += need;
+            }
+        }
+
+        // ------------------------------------------------------ housekeeping
+        round++;
+        if ((round & (HEARTBEAT_EVERY - 1)) == 0) {
+            flush_live();
+            if (lane == 0) atomicAdd(A.heartbeat, 1u);
+        }
+        // share work with idle warps: give away the oldest pending subtree
+        if ((round & 7) == 0 && top - bot >= 2) {
+            int want = 0;
+            if (lane == 0) {
+                const int idlew = ld_relaxed_i32(A.n_idle);
+                if (idlew > 0) {
+                    const unsigned long long qn = ld_relaxed(A.qtail) - ld_relaxed(A.qhead);
+                    if (qn < (unsigned long long)idlew) want = 1;
+                }
+            }
+            want = __shfl_sync(FULL, want, 0);
+            if (want) donate(min(2u, top - bot - 1));
+        }
+    }
+
+    // ------------------------------------------------------------ totals
+    flush_live();
+    for (int o = 16; o > 0; o >>= 1) {
+        nseg += __shfl_down_sync(FULL, nseg, o);
+        nrays += __shfl_down_sync(FULL, nrays, o);
+        nsplit += __shfl_down_sync(FULL, nsplit, o);
+        nterm += __shfl_down_sync(FULL, nterm, o);
+        nesc += __shfl_down_sync(FULL, nesc, o);
+        esc_photons += __shfl_down_sync(FULL, esc_photons, o);
+        maxlev = max(maxlev, __shfl_down_sync(FULL, maxlev, o));
+    }
+    if (lane == 0) {
+        atomicAdd(&A.counters[CNT_SEG], nseg);
+        atomicAdd(&A.counters[CNT_SEG_TOTAL], nseg);
+        atomicAdd(&A.counters[CNT_RAYS], nrays);
+        atomicAdd(&A.counters[CNT_SPLIT], nsplit);
+        atomicAdd(&A.counters[CNT_TERM], nterm);
+        atomicAdd(&A.counters[CNT_ESC], nesc);
+        atomicAdd(&A.counters[CNT_DONATE], ndon);
+        atomicMax(&A.counters[CNT_MAXLEVEL], (unsigned long long)maxlev);
+        if (esc_photons != 0.0) atomicAdd(A.escaped, esc_photons);
+    }
+}
+
+// ------------------------------------------------------------------ prep
+// absorber densities (Sec. 2.3) -> optical depth per cell length per group;
+// zero the accumulators (Sec. 2.1 step i).  One thread per internal cell.
+__global__ void k_prep(const PrepArgs P) {
+    const uint64_t nbc = (uint64_t)P.nb * P.nb * P.nb * 512ull;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nbc;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = q >> 9;
+        const uint32_t m = (uint32_t)(q & 511u);
+        const int k = (int)((b % P.nb) * 8 + compact3(m));
+        const int j = (int)(((b / P.nb) % P.nb) * 8 + compact3(m >> 1));
+        const int i = (int)((b / ((uint64_t)P.nb * P.nb)) * 8 + compact3(m >> 2));
+        float4 kap = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < P.n && j < P.n && k < P.n) {
+            const uint64_t c = ((uint64_t)i * P.n + j) * P.n + k;
+            const float nh = P.nH[c];
+            const float n0 = nh * P.xHI[c];
+            const float n1 = P.y * nh * P.xHeI[c];
+            const float n2 = P.y * nh * P.xHeII[c];
+            float kb[ARC_MAX_GROUPS];
+#pragma unroll
+            for (int g = 0; g < ARC_MAX_GROUPS; ++g)
+                kb[g] = (g < P.ng) ? (P.sig_dx[0][g] * n0 + P.sig_dx[1][g] * n1 + P.sig_dx[2][g] * n2) : 0.f;
+            kap = make_float4(kb[0], kb[1], kb[2], kb[3]);
+        }
+        P.kappa[q] = kap;
+        P.acc[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.acc[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void k_validate(const float* nH, const float* xHI, const float* xHeI, const float* xHeII,
+                           const float* T, long long ncell, unsigned int* status) {
+    bool bad = false;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float a = nH[c], b = xHI[c], d = xHeI[c], e = xHeII[c], t = T[c];
+        const bool ok = isfinite(a) && isfinite(b) && isfinite(d) && isfinite(e) && isfinite(t) &&
+                        a >= 0.f && b >= 0.f && b <= 1.f && d >= 0.f && d <= 1.f && e >= 0.f &&
+                        e <= 1.f && d + e <= 1.0f + 1e-6f && t > 0.f;
+        bad |= !ok;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ERR_FIELDS);
+}
+
+__global__ void k_make_seeds(const SourceDev* src, int nsrc, int per_src, int l_base, Entry* seeds) {
+    const long long total = (long long)nsrc * per_src;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(q / per_src), e = (int)(q % per_src);
+        Entry it;
+        it.key = make_key(4ull * (uint64_t)e, l_base, 0);
+        it.src = (uint32_t)s;
+        it.r = 0.0f;
+        it.N = src[s].N0;
+        seeds[q] = it;
+    }
+}
+
+__global__ void k_reset(TraceArgs A, unsigned long long qcap, int nseeds) {
+    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < qcap;
+         q += (unsigned long long)gridDim.x * blockDim.x)
+        A.qseq[q] = q;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *A.qhead = 0;
+        *A.qtail = 0;
+        *A.seed_head = 0;
+        *A.live = 4ll * nseeds;
+        *A.n_idle = 0;
+        *A.heartbeat = 0;
+        *A.escaped = 0.0;
+        for (int i = 0; i < CNT_N; ++i) A.counters[i] = 0;
+        A.counters[CNT_TRACES_TOTAL] += 1;
+        if (A.nrec) *A.nrec = 0;
+        atomicAnd(A.status, ~(ERR_TIMEOUT | ERR_QUEUE_FULL | ERR_RECORDS | ERR_CAS_SPIN));
+    }
+}
+
+// ------------------------------------------------------------------ finalize
+// Per cell: D_b photons absorbed in group b (compensated sum).  Eq. (ion)
+// splits D_b over the absorbers in proportion to sigma_{s,b} n_s and divides
+// by V n_s; with kappa_b = sum_s sigma_{s,b} n_s this is
+//   Gamma_s = (PHOT_UNIT / V) sum_b D_b sigma_{s,b} / kappa_b,
+// and the heating per absorber adds the excess energy E_b - E_s (Sec. 2.8).
+__global__ void k_finalize(const FinalizeArgs F) {
+    const uint64_t n3 = (uint64_t)F.n * F.n * F.n;
+    double part = 0.0;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n3;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(c % F.n);
+        const int j = (int)((c / F.n) % F.n);
+        const int i = (int)(c / ((uint64_t)F.n * F.n));
+        const uint64_t q = brick_index(i, j, k, F.nb);
+        const float4 hi = F.acc[2 * q], lo = F.acc[2 * q + 1];
+        part += ((double)hi.x + (double)lo.x) + ((double)hi.y + (double)lo.y) +
+                ((double)hi.z + (double)lo.z) + ((double)hi.w + (double)lo.w);
+        const float D[4] = {hi.x + lo.x, hi.y + lo.y, hi.z + lo.z, hi.w + lo.w};
+        const float nh = F.nH[c];
+        const float ns[3] = {nh * F.xHI[c], F.y * nh * F.xHeI[c], F.y * nh * F.xHeII[c]};
+        float g[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < ARC_MAX_GROUPS; ++b) {
+            if (b >= F.ng || D[b] == 0.f) continue;
+            const float kb = F.sig[0][b] * ns[0] + F.sig[1][b] * ns[1] + F.sig[2][b] * ns[2];
+            if (!(kb > 0.f)) continue;   // no absorber of this group in the cell
+            const float w = D[b] * F.scale;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const float rate = w * (F.sig[s][b] / kb);
+                g[s] += rate;
+                h[s] += rate * F.egap_erg[s][b];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            F.gamma[s * n3 + c] = g[s];
+            F.heat[s * n3 + c] = h[s];
+        }
+    }
+    // block partial of the absorbed photons
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(FULL, part, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        F.absorbed_part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_budget(const double* part, int nparts, const double* escaped, double* out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        out[0] = t;
+        out[1] = *escaped;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+int trace_smem_bytes(int block, int stack_log2) {
+    return (block / 32) * (1 << stack_log2) * (int)sizeof(Entry);
+}
+const void* trace_kernel_ptr() { return (const void*)k_trace; }
+
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
+    k_prep<<<152 * 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_validate(const float* nH, const float* xHI, const float* xHeI,
+                            const float* xHeII, const float* T, long long ncell,
+                            unsigned int* status, cudaStream_t s) {
+    k_validate<<<152 * 4, 256, 0, s>>>(nH, xHI, xHeI, xHeII, T, ncell, status);
+    return cudaGetLastError();
+}
+cudaError_t launch_make_seeds(const SourceDev* src, int nsrc, int l_base, Entry* seeds,
+                              cudaStream_t s) {
+    const int per_src = 3 << (2 * l_base);
+    const long long total = (long long)nsrc * per_src;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_make_seeds<<<blocks, 256, 0, s>>>(src, nsrc, per_src, l_base, seeds);
+    return cudaGetLastError();
+}
+cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s) {
+    k_reset<<<152 * 2, 256, 0, s>>>(a, qcap, nseeds);
+    return cudaGetLastError();
+}
+cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s) {
+    const int smem = trace_smem_bytes(block, a.stack_log2);
+    k_trace<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s) {
+    k_finalize<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_budget(const double* part, int nparts, const double* escaped, double* out,
+                          cudaStream_t s) {
+    k_budget<<<1, 256, 0, s>>>(part, nparts, escaped, out);
+    return cudaGetLastError();
+}
+
+}  // namespace arc

@@ -1,0 +1,114 @@
+"""GPU chemistry / energy update (libarc through the C ABI) against the FP64 oracle.
+
+Bars: neutral fractions within 1e-4 absolute of the oracle after every update
+and after free-running runs; temperature within 1e-3 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1807_07094_gb300 as P
+import workloads as W
+from helpers import gpu_trace, oracle_trace
+
+pytestmark = pytest.mark.gpu
+
+X_ATOL = 1e-4
+T_RTOL = 1e-3
+
+
+def gpu_chem_cells(params, nH, xHI, xHeI, xHeII, T, gamma, heat, dt):
+    """Run arc_chem_update on a flat set of cells laid out as an n^3 grid
+    (padded with empty cells)."""
+    ncell = nH.size
+    n = int(np.ceil(ncell ** (1 / 3)))
+    pad = n ** 3 - ncell
+    f = lambda a: np.concatenate([np.asarray(a, np.float32).ravel(), np.zeros(pad, np.float32)])
+    ft = lambda a: np.concatenate([np.asarray(a, np.float32).ravel(), np.ones(pad, np.float32) * 100])
+    with P.Arc(n, 1e21 * n, params) as a:
+        a.set_fields(f(nH).reshape(n, n, n), f(xHI).reshape(n, n, n), f(xHeI).reshape(n, n, n),
+                     f(xHeII).reshape(n, n, n), ft(T).reshape(n, n, n))
+        # rates go straight into the context's rate buffers
+        g, h, _ = a.trace(1.0, budget=False)
+        gg = torch.from_numpy(np.stack([f(gamma[s]) for s in range(3)]).reshape(3, n, n, n)).cuda()
+        hh = torch.from_numpy(np.stack([f(heat[s]) for s in range(3)]).reshape(3, n, n, n)).cuda()
+        g.copy_(gg)
+        h.copy_(hh)
+        torch.cuda.synchronize()
+        a.chem(dt)
+        out = a.get_fields()
+        st = a.stats()
+    return [o.ravel()[:ncell] for o in out], st
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_chem_random_cells(seed):
+    m = 4096
+    nH, xHI, xHeI, xHeII, T = W.random_gas(m, seed)
+    gamma, heat = W.random_rates(m, seed, gmax=1e-12)
+    p = W.thermal_128().params()
+    dt = 0.02 * W.MYR
+    (gx, gxe1, gxe2, gT), st = gpu_chem_cells(p, nH, xHI, xHeI, xHeII, T, gamma, heat, dt)
+    ox, oxe1, oxe2, oT, nsub, capped = oracle.chem(p, nH, xHI, xHeI, xHeII, T, gamma, heat, dt)
+    assert capped == 0 and st["chem_capped"] == 0
+    assert np.max(np.abs(gx - ox)) < X_ATOL
+    assert np.max(np.abs(gxe1 - oxe1)) < X_ATOL
+    assert np.max(np.abs(gxe2 - oxe2)) < X_ATOL
+    assert np.max(np.abs(gT / oT - 1)) < T_RTOL
+    assert st["chem_fp64_substeps"] > 0       # the x_HI < 1e-4 branch was exercised
+
+
+def test_chem_isothermal_fixed_alpha():
+    m = 2000
+    nH, xHI, _, _, T = W.random_gas(m, 5, Y=0.0)
+    T[:] = 1e4
+    gamma, heat = W.random_rates(m, 5, gmax=1e-11)
+    p = W.stromgren_32().params()
+    z = np.zeros(m, np.float32)
+    (gx, _, _, gT), st = gpu_chem_cells(p, nH, xHI, z, z, T, gamma, heat, 1.0 * W.MYR)
+    ox, _, _, oT, nsub, capped = oracle.chem(p, nH, xHI, z, z, T, gamma, heat, 1.0 * W.MYR)
+    assert np.max(np.abs(gx - ox)) < X_ATOL
+    assert np.all(gT == 1e4)
+
+
+def free_run_gpu(w, nsteps, use_graph):
+    with P.Arc(w.n, w.box_cm, w.params()) as a:
+        a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
+        a.add_sources(w.src_pos, w.src_ndot)
+        for k in range(nsteps):
+            if use_graph:
+                a.step(w.dt_s)
+            else:
+                a.trace(w.dt_s, budget=False)
+                a.chem(w.dt_s)
+        return a.get_fields()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_free_running_stromgren(use_graph):
+    """C1 run (32^3, 50 x 1 Myr): x after the run within 1e-4 of the oracle's."""
+    w = W.stromgren_32()
+    gx, _, _, _ = free_run_gpu(w, w.nsteps, use_graph)
+    ox, _, _, _, _ = oracle.run(w.params(), w, w.nsteps)
+    err = np.abs(gx - ox)
+    assert err.max() < X_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_free_running_thermal_short():
+    """H+He with heating/cooling (128^3 setup at 40^3), 10 steps of 0.5 Myr."""
+    w = W.thermal_128(n=40, box_kpc=6.6 * 40 / 128)
+    gx, gxe1, gxe2, gT = free_run_gpu(w, 10, True)
+    ox, oxe1, oxe2, oT, _ = oracle.run(w.params(), w, 10)
+    assert np.abs(gx - ox).max() < X_ATOL
+    assert np.abs(gxe1 - oxe1).max() < X_ATOL
+    assert np.abs(gxe2 - oxe2).max() < X_ATOL
+    assert np.abs(gT / oT - 1).max() < T_RTOL
+
+
+def test_graph_step_matches_eager():
+    w = W.cosmic(n=48, nsrc=8, seed=21)
+    a = free_run_gpu(w, 3, False)
+    b = free_run_gpu(w, 3, True)
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() <= 1e-6 * max(1.0, np.abs(x).max())

@@ -1,0 +1,136 @@
+"""GPU tracer (libarc through the C ABI) against the FP64 oracle, same seeded inputs.
+
+Bars (see tests/helpers.py): ray trees (split levels, end reasons, per-ray
+cell-visit counts) bit-exact outside the FP32 decision band; Gamma/heating
+relative 1e-4 where the oracle exceeds 1e-6 of its maximum; photon budget
+closed to 1e-9.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import (compare_records, gpu_trace, oracle_trace, partly_ionised, rate_errors,
+                     GAMMA_RTOL)
+
+pytestmark = pytest.mark.gpu
+
+
+def check_pair(w, xs=(None, None, None), records=True, rtol=GAMMA_RTOL, max_inband_frac=0.02):
+    g = gpu_trace(w, *xs, records=records)
+    o = oracle_trace(w, *xs, records=records)
+    launched, absorbed, escaped, emitted = g["budget"]
+    assert abs(launched - absorbed - escaped) <= 1e-9 * launched, g["budget"]
+    assert abs(launched - emitted) <= 1e-7 * emitted
+    em, ab, es = o["budget"]
+    assert abs(absorbed - ab) <= 1e-5 * em and abs(escaped - es) <= 1e-5 * em + 1e-300
+    assert g["stats"]["segments"] == sum(int(r["visits"]) for r in g["recs"]) if records else True
+    if records:
+        c = compare_records(g["recs"], o["recs"], w.n)
+        assert c["dup"] == 0
+        assert not c["mismatches"], c["mismatches"][:5]
+        assert not c["extra"], c["extra"][:5]
+        assert c["inband"] <= max_inband_frac * max(c["n_orc"], 1), c
+    for name in ("gamma", "heat"):
+        errs = rate_errors(g[name], o[name])
+        for s, (rel, cnt, rest) in enumerate(errs):
+            assert rel <= rtol, (name, s, rel, cnt)
+    return g, o
+
+
+def test_stromgren_initial_state():
+    w = W.stromgren_32()
+    g, o = check_pair(w)
+    assert g["stats"]["rays"] == len(o["recs"])
+
+
+def test_stromgren_partly_ionised_deep_tree():
+    w = W.stromgren_32()
+    xs = partly_ionised(w, seed=5, lo=-7, hi=-2)
+    g, o = check_pair(w, xs)
+    assert g["stats"]["max_level"] >= 5
+
+
+def test_h_he_three_groups_corner_source():
+    w = W.thermal_128(n=48, box_kpc=6.6 * 48 / 128)
+    xs = partly_ionised(w, seed=7, lo=-4, hi=0)
+    check_pair(w, xs)
+
+
+def test_cosmic_field_many_sources():
+    """Lognormal field, 16 uneven sources: the persistent queue, donation and
+    multi-source paths against the oracle."""
+    w = W.cosmic(n=64, nsrc=16, sigma_ln=1.5, seed=11)
+    xs = partly_ionised(w, seed=3, lo=-3, hi=0)
+    g, o = check_pair(w, xs)
+    assert g["stats"]["rays"] == len(o["recs"])
+
+
+def test_ragged_grid_and_plane_sources():
+    """n not a multiple of the 8-cell brick, sources exactly on cell planes,
+    at the box corner and with zero emission."""
+    w = W.thermal_128(n=20, box_kpc=6.6 * 20 / 128)
+    w.src_pos = np.array([[10.0, 10.0, 10.0], [0.0, 0.0, 0.0], [19.5, 3.0, 7.25], [5.0, 5.0, 5.0]])
+    w.src_ndot = np.vstack([w.src_ndot[0], w.src_ndot[0] * 0.3, w.src_ndot[0] * 2, 0 * w.src_ndot[0]])
+    xs = partly_ionised(w, seed=9, lo=-5, hi=-1)
+    check_pair(w, xs, max_inband_frac=0.05)
+
+
+def test_l_max_caps_the_tree():
+    w = W.stromgren_32()
+    p = w.params()
+    p["l_max"] = 2
+    xs = partly_ionised(w, seed=1, lo=-8, hi=-5)
+    g = gpu_trace(w, *xs, records=True, params=p)
+    o = oracle_trace(w, *xs, records=True, params=p)
+    assert g["stats"]["max_level"] == 2
+    c = compare_records(g["recs"], o["recs"], w.n)
+    assert not c["mismatches"] and not c["extra"]
+
+
+def test_no_sources_gives_zero_rates():
+    w = W.stromgren_32()
+    w.src_pos = np.zeros((0, 3))
+    w.src_ndot = np.zeros((0, 1))
+    g = gpu_trace(w)
+    assert np.all(g["gamma"] == 0) and np.all(g["heat"] == 0)
+    assert np.all(g["budget"] == 0)
+
+
+def test_source_scaling_invariance_gpu():
+    """N co-located sources of L/N reproduce one source of L (Sec. 4), to FP32."""
+    w = W.thermal_128(n=32, box_kpc=6.6 * 32 / 128)
+    xs = partly_ionised(w, seed=2, lo=-5, hi=-1)
+    w.src_pos = W.quantise_pos([[9.3, 17.6, 12.1]])
+    w.src_ndot = w.src_ndot * 20
+    g1 = gpu_trace(w, *xs)
+    w10 = W.subset_sources(w, [0] * 10)
+    w10.src_ndot = w10.src_ndot / 10
+    g10 = gpu_trace(w10, *xs)
+    for s in range(3):
+        o = g1["gamma"][s]
+        m = o > 1e-6 * o.max()
+        assert np.max(np.abs(g10["gamma"][s][m] / o[m] - 1)) < 1e-5
+
+
+def test_tuning_shapes_agree():
+    """Different launch shapes (block size, stack depth) give the same tree and
+    rates: the work decomposition does not change the result."""
+    w = W.cosmic(n=48, nsrc=8, sigma_ln=1.5, seed=4)
+    xs = partly_ionised(w, seed=8, lo=-4, hi=0)
+    a = gpu_trace(w, *xs, records=True, tuning=(256, 0, 64))
+    b = gpu_trace(w, *xs, records=True, tuning=(64, 2, 16))
+    ka = sorted(zip(a["recs"]["src"], a["recs"]["level"], a["recs"]["pix"], a["recs"]["visits"]))
+    kb = sorted(zip(b["recs"]["src"], b["recs"]["level"], b["recs"]["pix"], b["recs"]["visits"]))
+    assert ka == kb
+    for s in range(3):
+        o = a["gamma"][s]
+        m = o > 1e-6 * o.max()
+        assert np.max(np.abs(b["gamma"][s][m] / o[m] - 1)) < 1e-5
+
+
+@pytest.mark.parametrize("src", [[0, 12], [6, 10, 27]])
+def test_full_size_cosmic_256_sampled_sources(src):
+    """256^3 lognormal field at full size; a sample of its sources traced by
+    both sides (the whole 1000-source step is out of the oracle's reach)."""
+    w = W.subset_sources(W.cosmic_256(), src)
+    check_pair(w, records=True)
