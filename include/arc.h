@@ -15,9 +15,11 @@
  * Ownership  The context owns every device buffer it allocates; inputs are
  *            copied in.  Pointers returned by arc_trace stay valid until the
  *            next arc_trace or arc_destroy.
- * Streams    All work is queued on the stream given to arc_create (NULL = the
- *            legacy default stream).  Only the calls documented as
- *            synchronising wait for the GPU.
+ * Streams    All work is queued on the stream given to arc_create (NULL: the
+ *            context creates and owns a non-blocking stream).  Only the calls
+ *            documented as synchronising wait for the GPU; device outputs are
+ *            written on that stream, so a caller reading them on another
+ *            stream must synchronise first.
  * Errors     Every call returns an arc_status.  Errors found by a kernel
  *            (queue overflow, a bounded wait that gave up, a chemistry cell
  *            that hit the sub-step cap) are recorded in a device status word
@@ -119,7 +121,7 @@ typedef struct {
  * arc_create -- allocate a context for an n^3 grid (Sec. 2.3).
  *   out      receives the context (set to NULL on failure)
  *   g, p     grid and parameters, copied
- *   stream   cudaStream_t to queue all work on (NULL = legacy default stream)
+ *   stream   cudaStream_t to queue all work on (NULL: a private stream)
  * Allocates the field, rate, accumulator and work-queue buffers on the
  * current device.  Returns ARC_E_INVALID for out-of-range parameters,
  * ARC_E_OOM if an allocation fails.
@@ -206,8 +208,8 @@ arc_status arc_stats(arc_ctx* ctx, arc_stats_t* out);
 
 /*
  * arc_set_tuning -- launch shape of the persistent tracer: threads per block
- * (multiple of 32, 64..1024), blocks per SM (0 = occupancy limit) and local
- * work-stack entries per warp (power of two, 16..256).  0 keeps a value.
+ * (multiple of 32, 64..256), blocks per SM (0 = occupancy limit) and local
+ * work-stack entries per warp (power of two, 64..256).  0 keeps a value.
  */
 arc_status arc_set_tuning(arc_ctx* ctx, int block_threads, int blocks_per_sm, int stack_entries);
 

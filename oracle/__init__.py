@@ -57,11 +57,49 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
-def lib():
+class use_library:
+    """Temporarily route every oracle call to another build of arc_oracle.c
+    (used by the mutation tests, which plant a mistake in a copy)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = None
+        lib(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
+def build_variant(src_text: str, out_dir: str) -> str:
+    """Compile a modified copy of the oracle source into out_dir."""
+    c = os.path.join(out_dir, "arc_oracle.c")
+    with open(c, "w") as f:
+        f.write(src_text)
+    import shutil
+    shutil.copy(os.path.join(_HERE, "arc_oracle.h"), out_dir)
+    so = os.path.join(out_dir, "liborc_variant.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", so, c, "-lm"])
+    return so
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def lib(path: Optional[str] = None):
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB)
+        if path is None:
+            path = build()
+        L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         L.orc_pix2vec_nest.argtypes = [C.c_int, C.c_uint64, dp]
         L.orc_vec2pix_nest.argtypes = [C.c_int, dp]

@@ -240,6 +240,8 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
         double ds = r1 - r;
         if (ds < 0.0) ds = 0.0;
         if (isfinite(r_stop)) geo = fmin(geo, fabs(t - r_stop));
+        /* a face crossed right after a child's start is an undecided tie */
+        if (visits == 0 && r0 > 0.0) geo = fmin(geo, ds);
 
         /* Eq. (ion): absorb in every group */
         idx = ((int64_t)cell[0] * n + cell[1]) * n + cell[2];
@@ -279,12 +281,17 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
             break;
         }
         if (split) {
+            /* a face crossed right before the split distance is a near tie */
+            geo = fmin(geo, ds);
             end = ORC_END_SPLIT;
             break;
         }
         cell[ax] += (u[ax] > 0.0) ? 1 : -1;
         if (cell[ax] < 0 || cell[ax] >= n) {
             /* leaving the box: radiation is lost (Sec. 3.5) */
+            /* the exit face against the other faces: the one crossed just
+             * before (this segment's length) and the ones just after */
+            geo = fmin(geo, ds);
             for (int a = 0; a < 3; a++)
                 if (a != ax) geo = fmin(geo, fabs(tn[a] - t));
             for (int b = 0; b < G; b++) c->escaped += N[b];

@@ -51,6 +51,7 @@ struct arc_ctx {
     double box_cm = 0, dx = 0;
     arc_params p{};
     cudaStream_t stream = nullptr;
+    bool own_stream = false;      // created here when the caller passed NULL
     int device = 0, num_sms = 0;
     // fields (C order)
     float *nH = nullptr, *xHI = nullptr, *xHeI = nullptr, *xHeII = nullptr, *T = nullptr;
@@ -77,7 +78,7 @@ struct arc_ctx {
     arc_ray_rec* recs = nullptr;
     long long rec_cap = 0;
     bool fields_set = false, traced = false;
-    int block = 256, blocks_per_sm = 0, stack_log2 = 6;
+    int block = 256, blocks_per_sm = 0, stack_log2 = 7;
     float rsplit[ARC_MAX_LEVEL + 1] = {};
     cudaGraphExec_t gexec = nullptr;
     double graph_dt = -1.0;
@@ -381,6 +382,16 @@ arc_status arc_create(arc_ctx** out, const arc_grid* g, const arc_params* p, voi
         arc_destroy(c);
         return s;
     };
+    if (!c->stream) {
+        // a private stream: the legacy default stream cannot be captured into a graph
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(ARC_E_CUDA);
+        c->own_stream = true;
+    }
+    // allow the largest tuning (256 threads x 256 deque entries) once, for every context
+    if (cudaFuncSetAttribute(trace_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             trace_smem_bytes(256, 8)) != cudaSuccess)
+        return bail(ARC_E_CUDA);
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(ARC_E_CUDA);
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return bail(ARC_E_CUDA);
@@ -607,12 +618,10 @@ arc_status arc_set_tuning(arc_ctx* c, int block_threads, int blocks_per_sm, int 
     if (stack_entries) {
         int lg = 0;
         while ((1 << lg) < stack_entries) ++lg;
-        if ((1 << lg) != stack_entries || lg < 4 || lg > 8)
-            return fail(c, ARC_E_INVALID, "stack_entries must be a power of two in 16..256");
+        if ((1 << lg) != stack_entries || lg < 6 || lg > 8)
+            return fail(c, ARC_E_INVALID, "stack_entries must be a power of two in 64..256");
         c->stack_log2 = lg;
     }
-    const int smem = trace_smem_bytes(c->block, c->stack_log2);
-    CK(cudaFuncSetAttribute(trace_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     c->graph_valid = false;
     return ARC_OK;
 }
@@ -629,6 +638,7 @@ void arc_destroy(arc_ctx* c) {
     void* ptrs[] = {c->nH, c->xHI, c->xHeI, c->xHeII, c->T, c->kappa, c->acc, c->gamma, c->heat,
                     c->dsrc, c->seeds, c->qdata, c->qseq, c->scal, c->absorbed_part};
     for (void* q : ptrs) dfree(q);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 

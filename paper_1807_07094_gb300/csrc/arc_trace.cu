@@ -97,29 +97,33 @@ __device__ __forceinline__ float two_sum_err(float a, float b) {
     return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Eq. (ion) for one group: the fraction 1 - exp(-tau) of the ray's photons
-// is absorbed.  Returns the deposit D and updates N so that D + N_new equals
-// N_old exactly: whichever of the two is the larger is formed first and the
-// other as a Sterbenz-exact difference.
-__device__ __forceinline__ float absorb(float& N, float tau) {
+// Eq. (ion) for one group: the fraction 1 - exp(-tau) of the ray's photons is
+// absorbed.  The surviving photons are formed without cancellation
+// (N - N (1 - e^-tau) for small tau, N e^-tau for large tau), and the deposit
+// D = N_old - N_new is returned exactly as the unevaluated pair d + e (TwoSum),
+// so that D + N_new = N_old holds exactly in real arithmetic.
+__device__ __forceinline__ float absorb(float& N, float tau, float& e) {
     const float a = -expm1f(-tau);
-    const float A = __fmul_rn(N, a);
-    const float Nn = __fsub_rn(N, A);        // exact when a >= 1/2 (A in [N/2, N])
-    const float D = a >= 0.5f ? A : __fsub_rn(N, Nn);   // exact when a < 1/2 (Nn in [N/2, N])
+    const float Nn = (a < 0.5f) ? __fsub_rn(N, __fmul_rn(N, a)) : __fmul_rn(N, expf(-tau));
+    const float d = __fsub_rn(N, Nn);
+    const float bb = __fsub_rn(d, N);
+    e = __fadd_rn(__fsub_rn(N, __fsub_rn(d, bb)), __fsub_rn(-Nn, bb));
     N = Nn;
-    return D;
+    return d;
 }
 
-// compensated vector deposit into a cell's (hi, lo) accumulator pair
-__device__ __forceinline__ void deposit(float4* acc, uint64_t idx, float4 v) {
+// compensated vector deposit of D = d + e into a cell's (hi, lo) accumulator
+// pair: the atomic returns the old hi, the rounding error of old + d plus e
+// goes to lo.
+__device__ __forceinline__ void deposit(float4* acc, uint64_t idx, float4 d, float4 e) {
     float4* hi = acc + 2 * idx;
-    const float4 old = atom_add_v4(hi, v);
-    float4 e;
-    e.x = two_sum_err(old.x, v.x);
-    e.y = two_sum_err(old.y, v.y);
-    e.z = two_sum_err(old.z, v.z);
-    e.w = two_sum_err(old.w, v.w);
-    if (e.x != 0.f || e.y != 0.f || e.z != 0.f || e.w != 0.f) red_add_v4(hi + 1, e);
+    const float4 old = atom_add_v4(hi, d);
+    float4 l;
+    l.x = __fadd_rn(two_sum_err(old.x, d.x), e.x);
+    l.y = __fadd_rn(two_sum_err(old.y, d.y), e.y);
+    l.z = __fadd_rn(two_sum_err(old.z, d.z), e.z);
+    l.w = __fadd_rn(two_sum_err(old.w, d.w), e.w);
+    if (l.x != 0.f || l.y != 0.f || l.z != 0.f || l.w != 0.f) red_add_v4(hi + 1, l);
 }
 
 // ------------------------------------------------------------------ HEALPix
@@ -169,60 +173,90 @@ __device__ float3 healpix_dir(int level, uint64_t pix) {
 }
 
 // ------------------------------------------------------------------ work queue
-// Bounded multi-producer multi-consumer ring (one sequence word per slot): a
-// slot at position p is free for the producer when seq == p and holds data for
-// the consumer when seq == p + 1.  Both sides only retry a CAS; nothing waits
-// on another thread, so the operations are lock-free.
-__device__ bool q_push(const TraceArgs& A, const Entry& e) {
-    unsigned long long pos = ld_relaxed(A.qtail);
-    for (int it = 0; it < (1 << 20); ++it) {
-        unsigned long long* seq = &A.qseq[pos & A.qmask];
-        const unsigned long long s = ld_acquire(seq);
-        const long long dif = (long long)(s - pos);
-        if (dif == 0) {
-            if (atomicCAS(A.qtail, pos, pos + 1) == pos) {
-                Entry* d = &A.qdata[pos & A.qmask];
-                __stcg(reinterpret_cast<float4*>(d), *reinterpret_cast<const float4*>(&e));
-                __stcg(reinterpret_cast<float4*>(d) + 1, e.N);
-                st_release(seq, pos + 1);
-                return true;
+// Bounded multi-producer multi-consumer ring with one sequence word per slot:
+// the slot of position p is free for a producer when seq == p and holds data
+// for a consumer when seq == p + 1; a consumer frees it with seq = p + cap.
+// A warp reserves a run of consecutive slots with one CAS on tail (push) or
+// head (pop) after checking every slot of the run, so neither side ever waits
+// on another thread: the operations are lock-free and only retry the CAS.
+
+// Push the entries held by lanes 0..cnt-1 (cnt <= 32).  All lanes call.
+// Returns false (and flags ERR_QUEUE_FULL) if the ring has no room.
+__device__ bool q_push_warp(const TraceArgs& A, const Entry& e, unsigned cnt, int lane) {
+    if (cnt == 0) return true;
+    for (int it = 0; it < (1 << 16); ++it) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = ld_relaxed(A.qtail);
+        pos = __shfl_sync(FULL, pos, 0);
+        long long dif = 0;
+        if ((unsigned)lane < cnt) {
+            const unsigned long long p = pos + (unsigned long long)lane;
+            dif = (long long)(ld_acquire(&A.qseq[p & A.qmask]) - p);
+        }
+        const unsigned full = __ballot_sync(FULL, dif < 0);
+        if (full) {
+            atomicOr(A.status, ERR_QUEUE_FULL);
+            return false;
+        }
+        if (__ballot_sync(FULL, dif > 0)) continue;   // stale tail: re-read
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicCAS(A.qtail, pos, pos + cnt);
+        got = __shfl_sync(FULL, got, 0);
+        if (got == pos) {
+            if ((unsigned)lane < cnt) {
+                const unsigned long long p = pos + (unsigned long long)lane;
+                float4* d = reinterpret_cast<float4*>(&A.qdata[p & A.qmask]);
+                __stcg(d, *reinterpret_cast<const float4*>(&e));
+                __stcg(d + 1, e.N);
+                st_release(&A.qseq[p & A.qmask], p + 1);
             }
-            pos = ld_relaxed(A.qtail);
-        } else if (dif < 0) {
-            return false;   // full
-        } else {
-            pos = ld_relaxed(A.qtail);
+            return true;
         }
     }
     atomicOr(A.status, ERR_CAS_SPIN);
     return false;
 }
 
-__device__ bool q_pop(const TraceArgs& A, Entry& e) {
-    unsigned long long pos = ld_relaxed(A.qhead);
-    for (int it = 0; it < (1 << 20); ++it) {
-        unsigned long long* seq = &A.qseq[pos & A.qmask];
-        const unsigned long long s = ld_acquire(seq);
-        const long long dif = (long long)(s - (pos + 1));
-        if (dif == 0) {
-            if (atomicCAS(A.qhead, pos, pos + 1) == pos) {
-                const Entry* d = &A.qdata[pos & A.qmask];
-                const float4 a = __ldcg(reinterpret_cast<const float4*>(d));
-                const float4 b = __ldcg(reinterpret_cast<const float4*>(d) + 1);
-                *reinterpret_cast<float4*>(&e) = a;
-                e.N = b;
-                st_release(seq, pos + A.qmask + 1);
-                return true;
+// Pop up to `want` (<= 32) entries; lane i < (returned count) receives entry i.
+// All lanes call.  Returns 0 when nothing is published at the head.
+__device__ int q_pop_warp(const TraceArgs& A, Entry& e, int want, int lane) {
+    for (int it = 0; it < (1 << 16); ++it) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = ld_relaxed(A.qhead);
+        pos = __shfl_sync(FULL, pos, 0);
+        bool ready = false;
+        long long dif = -1;
+        if (lane < want) {
+            const unsigned long long p = pos + (unsigned long long)lane;
+            dif = (long long)(ld_acquire(&A.qseq[p & A.qmask]) - (p + 1));
+            ready = dif == 0;
+        }
+        const unsigned rm = __ballot_sync(FULL, ready);
+        const int c = (rm == FULL) ? 32 : (__ffs(~rm) - 1);   // consecutive ready slots from the head
+        if (c == 0) {
+            // slot at head not published: empty, or head is stale (dif > 0)
+            const int stale = __shfl_sync(FULL, (int)(dif > 0), 0);
+            if (stale) continue;
+            return 0;
+        }
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicCAS(A.qhead, pos, pos + (unsigned long long)c);
+        got = __shfl_sync(FULL, got, 0);
+        if (got == pos) {
+            if (lane < c) {
+                const unsigned long long p = pos + (unsigned long long)lane;
+                const float4* d = reinterpret_cast<const float4*>(&A.qdata[p & A.qmask]);
+                const float4 x = __ldcg(d);
+                const float4 y = __ldcg(d + 1);
+                *reinterpret_cast<float4*>(&e) = x;
+                e.N = y;
+                st_release(&A.qseq[p & A.qmask], p + A.qmask + 1);
             }
-            pos = ld_relaxed(A.qhead);
-        } else if (dif < 0) {
-            return false;   // empty (or the producer has not published yet)
-        } else {
-            pos = ld_relaxed(A.qhead);
+            return c;
         }
     }
     atomicOr(A.status, ERR_CAS_SPIN);
-    return false;
+    return 0;
 }
 
 // ------------------------------------------------------------------ ray state
@@ -287,19 +321,20 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
     const uint64_t idx = brick_index(R.cx, R.cy, R.cz, A.nb);
     const float4 kap = ldg_f4(&A.kappa[idx]);
     const float4 N0 = R.N;
-    float4 D;
-    D.x = absorb(R.N.x, kap.x * ds);
-    D.y = absorb(R.N.y, kap.y * ds);
-    D.z = absorb(R.N.z, kap.z * ds);
-    D.w = absorb(R.N.w, kap.w * ds);
+    float4 D, E;
+    D.x = absorb(R.N.x, kap.x * ds, E.x);
+    D.y = absorb(R.N.y, kap.y * ds, E.y);
+    D.z = absorb(R.N.z, kap.z * ds, E.z);
+    D.w = absorb(R.N.w, kap.w * ds, E.w);
     const float sumN = R.N.x + R.N.y + R.N.z + R.N.w;
     const bool term = sumN < R.thr;
     if (term) {
         // below threshold: every remaining photon stays in this cell
         D = N0;
+        E = make_float4(0.f, 0.f, 0.f, 0.f);
         R.N = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (D.x > 0.f || D.y > 0.f || D.z > 0.f || D.w > 0.f) deposit(A.acc, idx, D);
+    if (D.x > 0.f || D.y > 0.f || D.z > 0.f || D.w > 0.f) deposit(A.acc, idx, D, E);
     R.visits++;
     R.r = r1;
     if (term) return EV_TERM;
@@ -329,8 +364,8 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int cap = 1 << A.stack_log2;
-    const unsigned cmask = (unsigned)cap - 1u;
+    const unsigned cap = 1u << A.stack_log2;       // >= 64, so one round's pushes fit in half
+    const unsigned cmask = cap - 1u;
     Entry* stack = reinterpret_cast<Entry*>(smem_raw) + (size_t)wib * cap;
     const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -352,21 +387,43 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             live_delta = 0;
         }
     };
-    // move the oldest `cnt` local items to the global queue (all lanes call)
+    // move the oldest `cnt` items of the deque to the global ring (all lanes)
     auto donate = [&](unsigned cnt) {
         flush_live();   // rays made visible to other warps must be counted first
         __syncwarp();
         while (cnt > 0) {
             const unsigned chunk = cnt < 32u ? cnt : 32u;
-            if ((unsigned)lane < chunk) {
-                const Entry e = stack[(bot + lane) & cmask];
-                if (!q_push(A, e)) atomicOr(A.status, ERR_QUEUE_FULL);
-            }
+            Entry e;
+            if ((unsigned)lane < chunk) e = stack[(bot + lane) & cmask];
             __syncwarp();
+            if (!q_push_warp(A, e, chunk, lane)) break;   // ring full: keep them here
             bot += chunk;
             ndon += chunk;
             cnt -= chunk;
         }
+    };
+    // place up to `want` global items on the (empty) deque: donated subtrees
+    // first, then emitted items by ticket; returns the count (all lanes)
+    auto acquire = [&](int want) -> int {
+        Entry e;
+        const int c = q_pop_warp(A, e, want, lane);
+        if (c > 0) {
+            if (lane < c) stack[(top + lane) & cmask] = e;
+            __syncwarp();
+            return c;
+        }
+        unsigned t0 = 0;
+        int got = 0;
+        if (lane == 0 && ld_relaxed_u32(A.seed_head) < (unsigned)A.nseeds) {
+            t0 = atomicAdd(A.seed_head, (unsigned)want);
+            const int avail = A.nseeds - (int)t0;
+            got = avail <= 0 ? 0 : (avail < want ? avail : want);
+        }
+        got = __shfl_sync(FULL, got, 0);
+        t0 = __shfl_sync(FULL, t0, 0);
+        if (lane < got) stack[(top + lane) & cmask] = A.seeds[t0 + lane];
+        __syncwarp();
+        return got;
     };
 
     bool done = false;
@@ -374,92 +431,66 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
         // ---------------------------------------------------------------- refill
         unsigned idle = __ballot_sync(FULL, !active);
         if (idle) {
-            if (top == bot && (idle == FULL || (__popc(idle) >= 16 && (round & 3) == 0))) {
-                // local deque empty: fetch from the emitted items, then the ring
-                const bool all_idle = (idle == FULL);
-                int got = 0;   // items placed on the deque (warp-uniform)
-                int wanted = (__popc(idle) + 3) >> 2;
-                if (lane == 0) {
-                    unsigned t0 = 0;
-                    if (ld_relaxed_u32(A.seed_head) < (unsigned)A.nseeds) {
-                        t0 = atomicAdd(A.seed_head, (unsigned)wanted);
-                        int avail = A.nseeds - (int)t0;
-                        got = avail < 0 ? 0 : (avail < wanted ? avail : wanted);
-                    }
-                    if (got == 0) {
-                        Entry e;
-                        if (q_pop(A, e)) {
-                            stack[top & cmask] = e;
-                            got = -1;
-                        }
-                    } else {
-                        for (int i = 0; i < got; ++i) stack[(top + i) & cmask] = A.seeds[t0 + i];
-                    }
-                }
-                got = __shfl_sync(FULL, got, 0);
-                __syncwarp();
-                if (got < 0) {
-                    top += 1;
-                } else if (got > 0) {
-                    top += (unsigned)got;
-                } else if (all_idle) {
+            const int nidle = __popc(idle);
+            if (top == bot && (idle == FULL || (nidle >= 16 && (round & 3) == 0))) {
+                int got = acquire((nidle + 3) >> 2);
+                if (got == 0 && idle == FULL) {
                     // nothing anywhere for now: wait (bounded) for donations or the end
                     flush_live();
-                    int result = 0;   // 1 = got work, 2 = finished, 3 = gave up
-                    if (lane == 0) {
-                        atomicAdd(A.n_idle, 1);
-                        unsigned long long t_last = now_ns();
-                        unsigned hb_last = ld_relaxed_u32(A.heartbeat);
-                        long long live_last = ld_relaxed_s(A.live);
-                        unsigned sleep = 32;
-                        // bounded: 10 s (idle_timeout_ns) or 2^24 polls without any
-                        // sign of progress elsewhere ends the wait with an error
-                        for (unsigned poll = 0; poll < (1u << 24); ++poll) {
-                            Entry e;
-                            if (q_pop(A, e)) {
-                                stack[top & cmask] = e;
-                                result = 1;
-                                break;
-                            }
+                    __syncwarp();
+                    if (lane == 0) atomicAdd(A.n_idle, 1);
+                    unsigned long long t_last = now_ns();
+                    unsigned hb_last = ld_relaxed_u32(A.heartbeat);
+                    long long live_last = ld_relaxed_s(A.live);
+                    unsigned sleep = 32;
+                    int result = 0;   // 1 work, 2 finished, 3 gave up
+                    // bounded: 10 s (idle_timeout_ns) or 2^24 polls without any sign of
+                    // progress elsewhere end the wait with an error status
+                    for (unsigned poll = 0; poll < (1u << 24); ++poll) {
+                        got = acquire(8);
+                        if (got > 0) {
+                            result = 1;
+                            break;
+                        }
+                        int r = 0, progressed = 0;
+                        if (lane == 0) {
                             const long long lv = ld_relaxed_s(A.live);
-                            if (lv == 0) {
-                                result = 2;
-                                break;
-                            }
-                            if (ld_relaxed_u32(A.status) & (ERR_TIMEOUT | ERR_CAS_SPIN)) {
-                                result = 3;
-                                break;
-                            }
                             const unsigned hb = ld_relaxed_u32(A.heartbeat);
                             const unsigned long long tn = now_ns();
-                            if (hb != hb_last || lv != live_last) {
+                            if (lv == 0) {
+                                r = 2;
+                            } else if (ld_relaxed_u32(A.status) & (ERR_TIMEOUT | ERR_CAS_SPIN)) {
+                                r = 3;
+                            } else if (hb != hb_last || lv != live_last) {
                                 hb_last = hb;
                                 live_last = lv;
                                 t_last = tn;
-                                poll = 0;
+                                progressed = 1;
                             } else if (tn - t_last > A.idle_timeout_ns) {
                                 atomicOr(A.status, ERR_TIMEOUT);
-                                result = 3;
-                                break;
+                                r = 3;
                             }
-                            __nanosleep(sleep);
-                            if (sleep < 2048) sleep <<= 1;
                         }
-                        if (result == 0) {
-                            atomicOr(A.status, ERR_TIMEOUT);
-                            result = 3;
+                        r = __shfl_sync(FULL, r, 0);
+                        if (r) {
+                            result = r;
+                            break;
                         }
-                        atomicSub(A.n_idle, 1);
+                        if (__shfl_sync(FULL, progressed, 0)) poll = 0;
+                        __nanosleep(sleep);
+                        if (sleep < 2048) sleep <<= 1;
                     }
-                    result = __shfl_sync(FULL, result, 0);
-                    __syncwarp();
-                    if (result == 1) {
-                        top += 1;
-                    } else {
+                    if (result == 0) {
+                        if (lane == 0) atomicOr(A.status, ERR_TIMEOUT);
+                        result = 3;
+                    }
+                    if (lane == 0) atomicSub(A.n_idle, 1);
+                    if (result != 1) {
                         done = true;
                         break;
                     }
                 }
+                top += (unsigned)got;
             }
             // hand the children of the newest items to idle lanes (depth first)
             while (idle != 0 && top != bot) {
@@ -524,8 +555,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
                 }
             }
             const bool is_split = has_ev && ev == EV_SPLIT;
-            const bool is_end = has_ev && ev != EV_SPLIT;
-            if (is_end) {
+            if (has_ev && !is_split) {
                 if (ev == EV_ESC) {
                     esc_photons += (double)R.N.x + (double)R.N.y + (double)R.N.z + (double)R.N.w;
                     nesc++;
@@ -539,10 +569,15 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             const unsigned em = evm & ~sm;
             if (lane == 0) live_delta += 3 * (long long)__popc(sm) - (long long)__popc(em);
             if (sm) {
-                // make room: donate the oldest items if the deque would overflow
+                // make room: donate the oldest items if this round's pushes would not fit
                 const unsigned need = (unsigned)__popc(sm);
-                const unsigned size = top - bot;
-                if (size + need > (unsigned)cap) donate(size + need - (unsigned)cap / 2u);
+                if (top - bot + need > cap) donate(top - bot + need - cap / 2u);
+                const bool room = top - bot + need <= cap;
+                if (!room && lane == 0) {
+                    // ring and deque both full: these siblings are lost (flagged)
+                    live_delta -= 3 * (long long)need;
+                    atomicOr(A.status, ERR_QUEUE_FULL);
+                }
                 if (is_split) {
                     // children 1..3 wait on the deque; this lane continues with child 0
                     Entry e;
@@ -550,14 +585,14 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
                     e.src = R.src;
                     e.r = R.r;
                     e.N = make_float4(R.N.x * 0.25f, R.N.y * 0.25f, R.N.z * 0.25f, R.N.w * 0.25f);
-                    stack[(top + __popc(sm & lt_mask)) & cmask] = e;
+                    if (room) stack[(top + __popc(sm & lt_mask)) & cmask] = e;
                     nsplit++;
                     ev = start_ray(A, e, 0, R);
                     nrays++;
                     maxlev = max(maxlev, (unsigned)R.level);
                 }
                 __syncwarp();
-                top += need;
+                if (room) top += need;
             }
         }
 
@@ -567,7 +602,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             flush_live();
             if (lane == 0) atomicAdd(A.heartbeat, 1u);
         }
-        // share work with idle warps: give away the oldest pending subtree
+        // share work with idle warps: give away the oldest pending subtrees
         if ((round & 7) == 0 && top - bot >= 2) {
             int want = 0;
             if (lane == 0) {

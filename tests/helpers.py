@@ -121,7 +121,11 @@ def rate_errors(g_gpu, g_orc, floor=GAMMA_FLOOR):
             continue
         m = o > floor * mx
         rel = np.abs(g_gpu[s][m] - o[m]) / o[m]
-        out.append((float(rel.max()), int(m.sum()), float(np.abs(g_gpu[s][~m]).max(initial=0.0))))
+        i = int(np.argmax(rel))
+        worst = dict(rel=float(rel[i]), orc_over_max=float(o[m][i] / mx), gpu=float(g_gpu[s][m][i]),
+                     orc=float(o[m][i]), cell=np.argwhere(m)[i].tolist(),
+                     n_over_1e4=int((rel > 1e-4).sum()), n_over_1e3=int((rel > 1e-3).sum()))
+        out.append((float(rel.max()), int(m.sum()), worst))
     return out
 
 

@@ -31,6 +31,7 @@ def gpu_chem_cells(params, nH, xHI, xHeI, xHeII, T, gamma, heat, dt):
                      f(xHeII).reshape(n, n, n), ft(T).reshape(n, n, n))
         # rates go straight into the context's rate buffers
         g, h, _ = a.trace(1.0, budget=False)
+        torch.cuda.synchronize()   # the trace runs on the context's own stream
         gg = torch.from_numpy(np.stack([f(gamma[s]) for s in range(3)]).reshape(3, n, n, n)).cuda()
         hh = torch.from_numpy(np.stack([f(heat[s]) for s in range(3)]).reshape(3, n, n, n)).cuda()
         g.copy_(gg)

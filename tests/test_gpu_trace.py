@@ -27,13 +27,13 @@ def check_pair(w, xs=(None, None, None), records=True, rtol=GAMMA_RTOL, max_inba
     if records:
         c = compare_records(g["recs"], o["recs"], w.n)
         assert c["dup"] == 0
-        assert not c["mismatches"], c["mismatches"][:5]
+        assert not c["mismatches"], (len(c["mismatches"]), c["checked"], c["mismatches"][:5])
         assert not c["extra"], c["extra"][:5]
         assert c["inband"] <= max_inband_frac * max(c["n_orc"], 1), c
     for name in ("gamma", "heat"):
         errs = rate_errors(g[name], o[name])
-        for s, (rel, cnt, rest) in enumerate(errs):
-            assert rel <= rtol, (name, s, rel, cnt)
+        for s, (rel, cnt, worst) in enumerate(errs):
+            assert rel <= rtol, (name, s, cnt, worst, c if records else None)
     return g, o
 
 
@@ -109,7 +109,9 @@ def test_source_scaling_invariance_gpu():
     for s in range(3):
         o = g1["gamma"][s]
         m = o > 1e-6 * o.max()
-        assert np.max(np.abs(g10["gamma"][s][m] / o[m] - 1)) < 1e-5
+        rel = np.abs(g10["gamma"][s][m] / o[m] - 1)
+        i = int(np.argmax(rel))
+        assert rel[i] < 1e-5, (s, rel[i], o[m][i] / o.max(), int((rel > 1e-5).sum()), g1["budget"], g10["budget"])
 
 
 def test_tuning_shapes_agree():
@@ -118,7 +120,7 @@ def test_tuning_shapes_agree():
     w = W.cosmic(n=48, nsrc=8, sigma_ln=1.5, seed=4)
     xs = partly_ionised(w, seed=8, lo=-4, hi=0)
     a = gpu_trace(w, *xs, records=True, tuning=(256, 0, 64))
-    b = gpu_trace(w, *xs, records=True, tuning=(64, 2, 16))
+    b = gpu_trace(w, *xs, records=True, tuning=(64, 2, 256))
     ka = sorted(zip(a["recs"]["src"], a["recs"]["level"], a["recs"]["pix"], a["recs"]["visits"]))
     kb = sorted(zip(b["recs"]["src"], b["recs"]["level"], b["recs"]["pix"], b["recs"]["visits"]))
     assert ka == kb

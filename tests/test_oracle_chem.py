@@ -181,3 +181,17 @@ def test_stromgren_front_32():
             assert abs(r_i / r_an - 1) < GOLD["stromgren_agreement"]["tol"], (k, r_i, r_an)
         else:
             assert r_i < r_an * 1.05          # the fixed time step makes the front lag early
+
+
+def test_collisional_ionisation_equilibrium():
+    """No radiation, fixed T: hydrogen settles where collisional ionisation
+    balances recombination, x_HI = alpha / (alpha + beta)."""
+    for T in (1.5e4, 2.5e4, 5e4):
+        p = params(coll_ion=1, isothermal=1)
+        a, b = oracle.rates(p, T)[[0, 3]]
+        x_eq = a / (a + b)
+        nH = 1e-1
+        x, *_, capped = run_cell(p, nH, x_eq, 0.0, 0.0, T, [0, 0, 0], [0, 0, 0], 10 / (a * nH))
+        assert abs(x[0] - x_eq) < 1e-12
+        x, *_, capped = run_cell(p, nH, 0.5, 0.0, 0.0, T, [0, 0, 0], [0, 0, 0], 1e4 / (a * nH))
+        assert abs(x[0] - x_eq) < 2e-4, (T, x[0], x_eq)

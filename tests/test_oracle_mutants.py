@@ -1,0 +1,103 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each mutant is a copy of oracle/arc_oracle.c with one planted mistake (a
+dropped term, a wrong sign or index, a transposed operand, a wrong factor),
+compiled on the CPU and swapped in for the real oracle; at least one pin of
+tests/test_oracle_*.py must then fail.  Mistakes are planted only in the
+oracle, never in the CUDA path.
+"""
+import tempfile
+
+import pytest
+
+import oracle
+import test_oracle_chem as CH
+import test_oracle_healpix as HP
+import test_oracle_trace as TR
+
+# (name, original text, mutated text)
+MUTANTS = [
+    ("pix2vec swaps cos/sin", "v[0] = st * cos(phi);\n    v[1] = st * sin(phi);",
+     "v[0] = st * sin(phi);\n    v[1] = st * cos(phi);"),
+    ("pix2vec belt shift parity", "kshift = (int)((jr - ns) & 1);", "kshift = (int)((jr - ns + 1) & 1);"),
+    ("pix2vec south cap sign", "z = one_minus_z_or_plus - 1.0;", "z = 1.0 - one_minus_z_or_plus;"),
+    ("split radius without sqrt", "return 1.0 / sqrt(p->phi * omega);", "return 1.0 / (p->phi * omega);"),
+    ("ray keeps absorbed photons", "                N[b] -= A;\n", "\n"),
+    ("linearised absorption", "const double A = N[b] * (-expm1(-dtau));", "const double A = N[b] * dtau;"),
+    ("rate without cell length", "const double rate = A * p->sigma[s][b] * c->dx / (kappa_b * c->V);",
+     "const double rate = A * p->sigma[s][b] / (kappa_b * c->V);"),
+    ("transposed cell index", "idx = ((int64_t)cell[0] * n + cell[1]) * n + cell[2];",
+     "idx = ((int64_t)cell[2] * n + cell[1]) * n + cell[0];"),
+    ("always steps forward", "cell[ax] += (u[ax] > 0.0) ? 1 : -1;", "cell[ax] += 1;"),
+    ("children get half", "Nc[b] = N[b] / 4.0;", "Nc[b] = N[b] / 2.0;"),
+    ("residual dropped", "                    c->absorbed += N[b];\n                    if (kap[b] > 0.0) deposit(c, idx, b, N[b], kap[b]);\n",
+     "\n"),
+    ("threshold not scaled by level", "const double thr = c->thr_base / pow(4.0, level - p->l_base);",
+     "const double thr = c->thr_base;"),
+    ("heating sign of edge", "rate * (p->E_group_eV[b] - E_S[s]) * EVERG", "rate * (p->E_group_eV[b] + E_S[s]) * EVERG"),
+    ("escape not booked", "for (int b = 0; b < G; b++) c->escaped += N[b];\n            end = ORC_END_ESCAPE;\n            break;",
+     "end = ORC_END_ESCAPE;\n            break;"),
+    ("recombination on HI", "const double DH = r[0] * ne * nH;", "const double DH = r[0] * ne * nHI;"),
+    ("HeI source from HeI", "const double C1 = G1 + r[4] * ne, D1 = r[1] * ne * nHeII;",
+     "const double C1 = G1 + r[4] * ne, D1 = r[1] * ne * nHeI;"),
+    ("electrons miss HeIII", "const double ne = (nH - nHI) + nHeII + 2.0 * (nHe - nHeI - nHeII);",
+     "const double ne = (nH - nHI) + nHeII + (nHe - nHeI - nHeII);"),
+    ("energy factor", "E = 1.5 * KB * T * (nH + nHe + ne);", "E = 2.5 * KB * T * (nH + nHe + ne);"),
+    ("Compton sign", "Tg * Tg * Tg * Tg * (T - Tg) * ne", "Tg * Tg * Tg * Tg * (Tg - T) * ne"),
+    ("collisional sink dropped", "const double CH = G0 + (r[3] + r[0]) * ne;", "const double CH = G0 + r[0] * ne;"),
+    ("case-B exponent", "return 2.753e-14 * pow(lam, 1.5)", "return 2.753e-14 * pow(lam, 1.4)"),
+    ("limiter ignores n_HII", "const double lim = eps * fmax(fmin(nHI, nH - nHI), p->x_fp64 * nH);",
+     "const double lim = eps * fmax(nHI, p->x_fp64 * nH);"),
+]
+
+# fast pins first; a mutant is killed at the first failure
+PINS = [
+    lambda: HP.test_roundtrip(2),
+    lambda: HP.test_ring_latitudes_and_sizes(2),
+    lambda: HP.test_children_nest_inside_parent(1),
+    lambda: TR.test_uniform_medium_escape_closed_form((3.25, 10.5, 7.75)),
+    TR.test_budget_and_cell_sum_identity,
+    TR.test_clump_casts_sharp_shadow,
+    TR.test_energy_budget_of_heating,
+    lambda: TR.test_visit_counts_closed_form(0),
+    CH.test_case_b_alpha_matches_paper_test1,
+    lambda: CH.test_pure_h_equilibrium_quadratic(1e-3),
+    lambda: CH.test_pure_h_equilibrium_quadratic(0.3),
+    CH.test_h_he_photoionisation_equilibrium,
+    CH.test_recombination_decay,
+    CH.test_photoheating_of_neutral_gas_is_linear,
+    CH.test_compton_coefficient,
+    CH.test_collisional_ionisation_equilibrium,
+    TR.test_termination_distance_in_uniform_medium,
+    TR.test_rays_per_face_at_split_equals_phi,
+    TR.test_optically_thin_shells,
+]
+
+
+def killed(path):
+    with oracle.use_library(path):
+        for pin in PINS:
+            try:
+                pin()
+            except Exception:
+                return True
+    return False
+
+
+def test_every_mutant_is_killed():
+    src = oracle.source_text()
+    survivors = []
+    with tempfile.TemporaryDirectory() as d:
+        for name, old, new in MUTANTS:
+            assert src.count(old) == 1, f"mutation site not unique or missing: {name}"
+            sub = tempfile.mkdtemp(dir=d)
+            path = oracle.build_variant(src.replace(old, new), sub)
+            if not killed(path):
+                survivors.append(name)
+    assert not survivors, survivors
+
+
+def test_unmutated_oracle_passes_the_battery():
+    with tempfile.TemporaryDirectory() as d:
+        path = oracle.build_variant(oracle.source_text(), d)
+        assert not killed(path)
