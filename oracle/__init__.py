@@ -39,7 +39,7 @@ class OrcParams(C.Structure):
 
 REC_DTYPE = np.dtype([("src", "<u4"), ("level", "<i4"), ("pix", "<u8"), ("visits", "<i4"),
                       ("end", "<i4"), ("r0", "<f8"), ("r1", "<f8"), ("geo_margin", "<f8"),
-                      ("term_margin", "<f8")], align=True)
+                      ("term_margin", "<f8"), ("exit_margin", "<f8")], align=True)
 
 
 def build(force: bool = False) -> str:

@@ -207,7 +207,7 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
     const double* o = c->o;
 
     int cell[3];
-    double geo = INFINITY, term = INFINITY;
+    double geo = INFINITY, term = INFINITY, exitm = INFINITY;
     for (int a = 0; a < 3; a++) {
         const double x = o[a] + r0 * u[a];
         cell[a] = (int)floor(x);
@@ -239,7 +239,11 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
         const double r1 = split ? r_stop : t;
         double ds = r1 - r;
         if (ds < 0.0) ds = 0.0;
-        if (isfinite(r_stop)) geo = fmin(geo, fabs(t - r_stop));
+        if (isfinite(r_stop)) {
+            geo = fmin(geo, fabs(t - r_stop));
+            const int nxt = cell[ax] + ((u[ax] > 0.0) ? 1 : -1);
+            if (nxt < 0 || nxt >= n) exitm = fmin(exitm, fabs(t - r_stop));
+        }
         /* a face crossed right after a child's start is an undecided tie */
         if (visits == 0 && r0 > 0.0) geo = fmin(geo, ds);
 
@@ -312,6 +316,7 @@ record:
             q->r1 = r;
             q->geo_margin = geo;
             q->term_margin = term;
+            q->exit_margin = exitm;
         } else {
             c->overflow = 1;
         }

@@ -57,8 +57,11 @@ typedef struct {
     int32_t  visits;     /* cell segments traced (zero-length ones included)     */
     int32_t  end;        /* ORC_END_*                                            */
     double   r0, r1;     /* start / end distance from the source [cells]         */
-    double   geo_margin; /* smallest distance of a geometric decision to a tie   */
+    double   geo_margin; /* smallest distance of a geometric decision that sets
+                            this ray's own visit count to a tie [cells]         */
     double   term_margin;/* smallest |sum N - threshold| / threshold             */
+    double   exit_margin;/* |t - r_split| for a box-exit face near the split
+                            distance: decides whether children exist [cells]    */
 } orc_ray_rec;
 
 /* HEALPix nested scheme (Gorski et al. 2005): pixel centre -> unit vector. */

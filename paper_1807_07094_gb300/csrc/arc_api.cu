@@ -226,6 +226,17 @@ arc_status upload_sources(arc_ctx* c) {
     return ARC_OK;
 }
 
+// Events inside a captured graph must be external record nodes; outside a
+// capture they are plain records.
+cudaError_t record_event(arc_ctx* c, cudaEvent_t ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive)
+        return cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal);
+    return cudaEventRecord(ev, c->stream);
+}
+
 TraceArgs trace_args(arc_ctx* c) {
     TraceArgs a;
     memset(&a, 0, sizeof a);
@@ -295,9 +306,9 @@ arc_status enqueue_trace(arc_ctx* c) {
     CK(launch_prep(P, c->stream));
     TraceArgs A = trace_args(c);
     CK(launch_seed_reset(A, c->qcap, c->nseeds, c->stream));
-    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(record_event(c, c->ev[0]));
     if (c->nseeds > 0) CK(launch_trace(A, trace_grid(c), c->block, c->stream));
-    CK(cudaEventRecord(c->ev[1], c->stream));
+    CK(record_event(c, c->ev[1]));
     FinalizeArgs F;
     memset(&F, 0, sizeof F);
     F.n = c->n;
@@ -352,9 +363,9 @@ arc_status enqueue_chem(arc_ctx* c, double dt) {
     C.status = &c->scal->status;
     C.counters = c->scal->chem_counters;
     CK(cudaMemsetAsync(c->scal->chem_counters, 0, sizeof(c->scal->chem_counters), c->stream));
-    CK(cudaEventRecord(c->ev[2], c->stream));
+    CK(record_event(c, c->ev[2]));
     CK(launch_chem(C, c->stream));
-    CK(cudaEventRecord(c->ev[3], c->stream));
+    CK(record_event(c, c->ev[3]));
     return ARC_OK;
 }
 

@@ -97,19 +97,42 @@ __device__ __forceinline__ float two_sum_err(float a, float b) {
     return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Eq. (ion) for one group: the fraction 1 - exp(-tau) of the ray's photons is
-// absorbed.  The surviving photons are formed without cancellation
-// (N - N (1 - e^-tau) for small tau, N e^-tau for large tau), and the deposit
-// D = N_old - N_new is returned exactly as the unevaluated pair d + e (TwoSum),
-// so that D + N_new = N_old holds exactly in real arithmetic.
-__device__ __forceinline__ float absorb(float& N, float tau, float& e) {
+// Eq. (ion) for one group: the fraction a = 1 - exp(-tau) of the ray's
+// photons is absorbed.  The ray carries its photons as an unevaluated pair
+// Nh + Nl, so that it can lose exactly what the cell receives without the
+// loss being rounded to a multiple of ulp(Nh) (which would make thin-cell
+// deposits, a ~ 1e-5, wrong by ~6e-8/a).  The deposit is returned as the pair
+// d + e and Nh + Nl + d + e is conserved up to ~2^-48 Nh per segment:
+//   thin (a < 1/2): d = fl(Nh a), the ray subtracts d exactly;
+//   thick:          the survivors fl(Nh e^-tau) are formed directly (no
+//                   cancellation) and d + e is the exact difference.
+__device__ __forceinline__ void absorb(float& Nh, float& Nl, float tau, float& d, float& e) {
     const float a = -expm1f(-tau);
-    const float Nn = (a < 0.5f) ? __fsub_rn(N, __fmul_rn(N, a)) : __fmul_rn(N, expf(-tau));
-    const float d = __fsub_rn(N, Nn);
-    const float bb = __fsub_rn(d, N);
-    e = __fadd_rn(__fsub_rn(N, __fsub_rn(d, bb)), __fsub_rn(-Nn, bb));
-    N = Nn;
-    return d;
+    if (a < 0.5f) {
+        d = __fmul_rn(Nh, a);
+        e = 0.0f;
+        const float s = __fsub_rn(Nh, d);                 // TwoSum(Nh, -d) = (s, r)
+        const float bb = __fsub_rn(s, Nh);
+        const float r = __fadd_rn(__fsub_rn(Nh, __fsub_rn(s, bb)), __fsub_rn(-d, bb));
+        const float lo = __fadd_rn(Nl, r);
+        Nh = __fadd_rn(s, lo);                            // renormalise (|lo| << |s|)
+        Nl = __fsub_rn(lo, __fsub_rn(Nh, s));
+    } else {
+        const float Nn = __fmul_rn(Nh, expf(-tau));
+        d = __fsub_rn(Nh, Nn);                            // TwoSum(Nh, -Nn) = (d, r)
+        const float bb = __fsub_rn(d, Nh);
+        const float r = __fadd_rn(__fsub_rn(Nh, __fsub_rn(d, bb)), __fsub_rn(-Nn, bb));
+        e = __fadd_rn(r, Nl);
+        Nh = Nn;
+        Nl = 0.0f;
+    }
+}
+
+// (Nh, Nl) <- Nh + lo as a normalised pair (|lo| within a few ulps of Nh)
+__device__ __forceinline__ void fold_low(float& Nh, float& Nl, float lo) {
+    const float s = __fadd_rn(Nh, lo);
+    Nl = __fsub_rn(lo, __fsub_rn(s, Nh));
+    Nh = s;
 }
 
 // compensated vector deposit of D = d + e into a cell's (hi, lo) accumulator
@@ -268,7 +291,8 @@ struct Ray {
     float tx, ty, tz;      // distance to the next plane per axis
     int cx, cy, cz;        // current cell
     float r, rstop, thr;
-    float4 N;
+    float4 N;              // photons per group (high part)
+    float4 Nl;             // low part: the photons are N + Nl
     uint64_t pix;
     uint32_t src;
     int level;
@@ -288,6 +312,7 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
     R.src = e.src;
     R.r = e.r;
     R.N = e.N;
+    R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     R.visits = 0;
     const SourceDev* S = &A.src[e.src];
     const float4 pt = __ldg(&S->pos_thr);
@@ -320,21 +345,24 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
     const float ds = fmaxf(r1 - R.r, 0.0f);
     const uint64_t idx = brick_index(R.cx, R.cy, R.cz, A.nb);
     const float4 kap = ldg_f4(&A.kappa[idx]);
-    const float4 N0 = R.N;
+    const float4 Nh0 = R.N, Nl0 = R.Nl;
     float4 D, E;
-    D.x = absorb(R.N.x, kap.x * ds, E.x);
-    D.y = absorb(R.N.y, kap.y * ds, E.y);
-    D.z = absorb(R.N.z, kap.z * ds, E.z);
-    D.w = absorb(R.N.w, kap.w * ds, E.w);
+    absorb(R.N.x, R.Nl.x, kap.x * ds, D.x, E.x);
+    absorb(R.N.y, R.Nl.y, kap.y * ds, D.y, E.y);
+    absorb(R.N.z, R.Nl.z, kap.z * ds, D.z, E.z);
+    absorb(R.N.w, R.Nl.w, kap.w * ds, D.w, E.w);
     const float sumN = R.N.x + R.N.y + R.N.z + R.N.w;
     const bool term = sumN < R.thr;
     if (term) {
         // below threshold: every remaining photon stays in this cell
-        D = N0;
-        E = make_float4(0.f, 0.f, 0.f, 0.f);
+        D = Nh0;
+        E = Nl0;
         R.N = make_float4(0.f, 0.f, 0.f, 0.f);
+        R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (D.x > 0.f || D.y > 0.f || D.z > 0.f || D.w > 0.f) deposit(A.acc, idx, D, E);
+    if (D.x != 0.f || D.y != 0.f || D.z != 0.f || D.w != 0.f || E.x != 0.f || E.y != 0.f ||
+        E.z != 0.f || E.w != 0.f)
+        deposit(A.acc, idx, D, E);
     R.visits++;
     R.r = r1;
     if (term) return EV_TERM;
@@ -557,7 +585,8 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             const bool is_split = has_ev && ev == EV_SPLIT;
             if (has_ev && !is_split) {
                 if (ev == EV_ESC) {
-                    esc_photons += (double)R.N.x + (double)R.N.y + (double)R.N.z + (double)R.N.w;
+                    esc_photons += ((double)R.N.x + (double)R.Nl.x) + ((double)R.N.y + (double)R.Nl.y) +
+                                   ((double)R.N.z + (double)R.Nl.z) + ((double)R.N.w + (double)R.Nl.w);
                     nesc++;
                 } else {
                     nterm++;
@@ -587,7 +616,15 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
                     e.N = make_float4(R.N.x * 0.25f, R.N.y * 0.25f, R.N.z * 0.25f, R.N.w * 0.25f);
                     if (room) stack[(top + __popc(sm & lt_mask)) & cmask] = e;
                     nsplit++;
+                    // children 1..3 carry exact FP32 quarters; child 0 (this lane)
+                    // also inherits the parent's sub-ulp low part, so no photon
+                    // is lost and no cell receives a spurious deposit
+                    const float4 keep = R.Nl;
                     ev = start_ray(A, e, 0, R);
+                    fold_low(R.N.x, R.Nl.x, keep.x);
+                    fold_low(R.N.y, R.Nl.y, keep.y);
+                    fold_low(R.N.z, R.Nl.z, keep.z);
+                    fold_low(R.N.w, R.Nl.w, keep.w);
                     nrays++;
                     maxlev = max(maxlev, (unsigned)R.level);
                 }

@@ -68,19 +68,31 @@ def geo_band(r, n):
 
 
 def compare_records(gpu_recs, orc_recs, n):
-    """Compare ray trees.  Returns dict(checked, inband, mismatches)."""
+    """Compare ray trees key by key (source, level, pixel).
+
+    A ray whose own visit count rests on an undecided tie (oracle geometric
+    margin inside the band) may differ by that count only; a ray whose fate
+    rests on one (photon threshold, or a box exit at the split distance) may
+    also have a different subtree, so its descendants are not compared.
+    Returns counts and the mismatching keys."""
     orc = {}
-    inband = set()
+    fate = set()
+    own = set()
     for a in orc_recs:
         key = (int(a["src"]), int(a["level"]), int(a["pix"]))
         orc[key] = a
-        if a["geo_margin"] < geo_band(a["r1"], n) or a["term_margin"] < TERM_BAND:
-            inband.add(key)
+        band = geo_band(a["r1"], n)
+        if a["term_margin"] < TERM_BAND or a["exit_margin"] < band:
+            fate.add(key)
+        elif a["geo_margin"] < band:
+            own.add(key)
 
-    def ancestor_inband(key):
+    def ancestor_fate(key):
         s, l, p = key
+        l -= 1
+        p >>= 2
         while l >= 1:
-            if (s, l, p) in inband:
+            if (s, l, p) in fate:
                 return True
             l -= 1
             p >>= 2
@@ -96,17 +108,24 @@ def compare_records(gpu_recs, orc_recs, n):
     mism = []
     checked = skipped = 0
     for key, a in orc.items():
-        if ancestor_inband(key):
+        if ancestor_fate(key):
             skipped += 1
             continue
         b = gpu.get(key)
+        if key in fate or key in own:
+            # undecided: the ray must exist; its count/end may differ
+            if b is None and key in own:
+                mism.append((key, None, "missing"))
+            skipped += 1
+            continue
         if b is None or int(b["visits"]) != int(a["visits"]) or int(b["end"]) != int(a["end"]):
             mism.append((key, None if b is None else (int(b["visits"]), int(b["end"])),
-                         (int(a["visits"]), int(a["end"]), float(a["geo_margin"]), float(a["term_margin"]))))
+                         (int(a["visits"]), int(a["end"]), float(a["geo_margin"]),
+                          float(a["term_margin"]), float(a["exit_margin"]))))
         checked += 1
-    extra = [k for k in gpu if k not in orc and not ancestor_inband(k)]
-    return dict(checked=checked, inband=skipped, mismatches=mism, extra=extra, dup=dup,
-                n_gpu=len(gpu_recs), n_orc=len(orc_recs))
+    extra = [k for k in gpu if k not in orc and not ancestor_fate(k)]
+    return dict(checked=checked, undecided=len(fate) + len(own), skipped=skipped,
+                mismatches=mism, extra=extra, dup=dup, n_gpu=len(gpu_recs), n_orc=len(orc_recs))
 
 
 def rate_errors(g_gpu, g_orc, floor=GAMMA_FLOOR):

@@ -79,6 +79,7 @@ def blackbody_groups(t_bb: float = 1.0e5, edges_ev=(13.6, 24.6, 54.4, 544.0),
     for b in range(g):
         lo, hi = edges_ev[b], edges_ev[b + 1]
         e = np.linspace(lo, hi, nquad + 1)
+        e[-1] = hi * (1.0 - 1e-12)          # the group is [lo, hi): the next edge is excluded
         x = e / kt_ev
         nphot = x * x / np.expm1(x)          # photons per unit x (Planck)
         w = np.ones(nquad + 1)
@@ -192,7 +193,7 @@ def gaussian_field_k3(n: int, rng: np.random.Generator) -> np.ndarray:
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (-0.75)                  # |k|^{-3/2}
-    d = np.fft.irfftn(wk * amp, s=(n, n, n))
+    d = np.fft.irfftn(wk * amp, s=(n, n, n), axes=(0, 1, 2))
     d -= d.mean()
     d /= d.std()
     return d
