@@ -196,6 +196,9 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     w = W.cosmic_256()
+    if args.sources != w.nsrc:
+        # profiling aid: the same field with only the first N sources
+        w = W.subset_sources(w, list(range(args.sources)))
     p = w.params()
     stream = torch.cuda.Stream()
     a = P.Arc(w.n, w.box_cm, p, stream=stream.cuda_stream)
@@ -247,7 +250,7 @@ def run_ours(args):
     pinned = [torch.empty(n3, dtype=torch.float32).pin_memory() for _ in range(5)]
     for t, src in zip(pinned, (w.nH, w.xHI, w.xHeI, w.xHeII, w.T)):
         t.numpy()[:] = src.ravel()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
     segs_e0 = a.stats()["segments_total"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -255,7 +258,7 @@ def run_ours(args):
         a.set_fields(*[t.numpy().reshape(w.nH.shape) for t in pinned])
         a.step(w.dt_s)
         P.arc_get_fields(a.ctx, *[t.numpy().reshape(w.nH.shape) for t in pinned[1:]])
-    t_e2e = time.perf_counter() - t0
+    t_e2e = max(time.perf_counter() - t0, 1e-9)
     segs_e2e = a.stats()["segments_total"] - segs_e0
     a.close()
 
@@ -308,6 +311,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", type=int, default=1000,
+                    help="profiling aid: trace only the first N sources of the workload")
+    ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the e2e pass")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

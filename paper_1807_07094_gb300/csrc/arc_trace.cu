@@ -204,10 +204,15 @@ __device__ float3 healpix_dir(int level, uint64_t pix) {
 // on another thread: the operations are lock-free and only retry the CAS.
 
 // Push the entries held by lanes 0..cnt-1 (cnt <= 32).  All lanes call.
-// Returns false (and flags ERR_QUEUE_FULL) if the ring has no room.
-__device__ bool q_push_warp(const TraceArgs& A, const Entry& e, unsigned cnt, int lane) {
+// A mandatory push (the deque overflows) retries up to 2^20 times and flags
+// ERR_QUEUE_FULL / ERR_CAS_SPIN on failure; an optional one (sharing work
+// with idle warps) gives up quietly after a few lost races.  Returns whether
+// the entries were pushed.
+__device__ bool q_push_warp(const TraceArgs& A, const Entry& e, unsigned cnt, int lane,
+                            bool mandatory) {
     if (cnt == 0) return true;
-    for (int it = 0; it < (1 << 16); ++it) {
+    const int tries = mandatory ? (1 << 20) : 16;
+    for (int it = 0; it < tries; ++it) {
         unsigned long long pos = 0;
         if (lane == 0) pos = ld_relaxed(A.qtail);
         pos = __shfl_sync(FULL, pos, 0);
@@ -218,14 +223,18 @@ __device__ bool q_push_warp(const TraceArgs& A, const Entry& e, unsigned cnt, in
         }
         const unsigned full = __ballot_sync(FULL, dif < 0);
         if (full) {
-            atomicOr(A.status, ERR_QUEUE_FULL);
+            if (mandatory && lane == 0) atomicOr(A.status, ERR_QUEUE_FULL);
             return false;
         }
         if (__ballot_sync(FULL, dif > 0)) continue;   // stale tail: re-read
         unsigned long long got = 0;
         if (lane == 0) got = atomicCAS(A.qtail, pos, pos + cnt);
         got = __shfl_sync(FULL, got, 0);
-        if (got == pos) {
+        if (got != pos) {
+            __nanosleep(64u << (it & 3));   // lost the race to another producer
+            continue;
+        }
+        {
             if ((unsigned)lane < cnt) {
                 const unsigned long long p = pos + (unsigned long long)lane;
                 float4* d = reinterpret_cast<float4*>(&A.qdata[p & A.qmask]);
@@ -236,14 +245,16 @@ __device__ bool q_push_warp(const TraceArgs& A, const Entry& e, unsigned cnt, in
             return true;
         }
     }
-    atomicOr(A.status, ERR_CAS_SPIN);
+    if (mandatory && lane == 0) atomicOr(A.status, ERR_CAS_SPIN);
     return false;
 }
 
 // Pop up to `want` (<= 32) entries; lane i < (returned count) receives entry i.
-// All lanes call.  Returns 0 when nothing is published at the head.
+// All lanes call.  Returns 0 when nothing is published at the head, or after a
+// few lost races with other consumers (each loss is another warp's progress;
+// the caller polls again later).
 __device__ int q_pop_warp(const TraceArgs& A, Entry& e, int want, int lane) {
-    for (int it = 0; it < (1 << 16); ++it) {
+    for (int it = 0; it < 32; ++it) {
         unsigned long long pos = 0;
         if (lane == 0) pos = ld_relaxed(A.qhead);
         pos = __shfl_sync(FULL, pos, 0);
@@ -265,7 +276,11 @@ __device__ int q_pop_warp(const TraceArgs& A, Entry& e, int want, int lane) {
         unsigned long long got = 0;
         if (lane == 0) got = atomicCAS(A.qhead, pos, pos + (unsigned long long)c);
         got = __shfl_sync(FULL, got, 0);
-        if (got == pos) {
+        if (got != pos) {
+            __nanosleep(64u << (it & 3));   // lost the race: back off a little
+            continue;
+        }
+        {
             if (lane < c) {
                 const unsigned long long p = pos + (unsigned long long)lane;
                 const float4* d = reinterpret_cast<const float4*>(&A.qdata[p & A.qmask]);
@@ -278,7 +293,6 @@ __device__ int q_pop_warp(const TraceArgs& A, Entry& e, int want, int lane) {
             return c;
         }
     }
-    atomicOr(A.status, ERR_CAS_SPIN);
     return 0;
 }
 
@@ -416,7 +430,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
         }
     };
     // move the oldest `cnt` items of the deque to the global ring (all lanes)
-    auto donate = [&](unsigned cnt) {
+    auto donate = [&](unsigned cnt, bool mandatory) {
         flush_live();   // rays made visible to other warps must be counted first
         __syncwarp();
         while (cnt > 0) {
@@ -424,7 +438,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             Entry e;
             if ((unsigned)lane < chunk) e = stack[(bot + lane) & cmask];
             __syncwarp();
-            if (!q_push_warp(A, e, chunk, lane)) break;   // ring full: keep them here
+            if (!q_push_warp(A, e, chunk, lane, mandatory)) break;   // not pushed: keep them here
             bot += chunk;
             ndon += chunk;
             cnt -= chunk;
@@ -600,7 +614,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             if (sm) {
                 // make room: donate the oldest items if this round's pushes would not fit
                 const unsigned need = (unsigned)__popc(sm);
-                if (top - bot + need > cap) donate(top - bot + need - cap / 2u);
+                if (top - bot + need > cap) donate(top - bot + need - cap / 2u, true);
                 const bool room = top - bot + need <= cap;
                 if (!room && lane == 0) {
                     // ring and deque both full: these siblings are lost (flagged)
@@ -640,7 +654,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
             if (lane == 0) atomicAdd(A.heartbeat, 1u);
         }
         // share work with idle warps: give away the oldest pending subtrees
-        if ((round & 7) == 0 && top - bot >= 2) {
+        if ((round & 15) == 0 && top - bot >= 2) {
             int want = 0;
             if (lane == 0) {
                 const int idlew = ld_relaxed_i32(A.n_idle);
@@ -650,7 +664,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
                 }
             }
             want = __shfl_sync(FULL, want, 0);
-            if (want) donate(min(2u, top - bot - 1));
+            if (want) donate(min(2u, top - bot - 1), false);
         }
     }
 
