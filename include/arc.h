@@ -213,6 +213,40 @@ arc_status arc_stats(arc_ctx* ctx, arc_stats_t* out);
  */
 arc_status arc_set_tuning(arc_ctx* ctx, int block_threads, int blocks_per_sm, int stack_entries);
 
+/*
+ * arc_trace_noalloc -- one radiative-transfer pass, like arc_trace, that
+ * allocates nothing.  For callers that cannot allocate device memory at the
+ * time of the call: code running while a stream is captured into a CUDA graph
+ * (cudaMalloc/cudaFree are not permitted there, and cudaFree synchronises the
+ * device), and applications that reserve all device memory up front.  The
+ * paper has no counterpart; this is a deployment variant of the tracer.
+ *
+ *   g, p            grid and parameters as for arc_create; n <= ARC_NOALLOC_MAX_N,
+ *                   l_base <= 2
+ *   nH..xHeII       device pointers, n^3 FP32 each, C order (as arc_set_fields)
+ *   nsrc, pos, ndot host arrays as for arc_add_sources, nsrc <= ARC_NOALLOC_MAX_SOURCES
+ *   gamma, heat     caller-owned device buffers of 3 n^3 FP32 each (outputs, as
+ *                   returned by arc_trace)
+ *   budget          NULL or host double[4], as for arc_trace
+ *   stream          cudaStream_t for the work (NULL = legacy default stream)
+ *
+ * Scratch memory is one fixed file-scope device array of about 22 MB that every
+ * device which loads libarc holds until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (each call clears what must start at zero), so
+ * calls whose GPU work overlaps -- on different streams or from different host
+ * threads -- race and corrupt each other's results.  Synchronises the stream.
+ * Returns ARC_E_INVALID for sizes beyond the maximum or bad arguments, and the
+ * tracer errors of arc_trace (ARC_E_TIMEOUT, ARC_E_OVERFLOW, ARC_E_BUDGET).
+ */
+#define ARC_NOALLOC_MAX_N 64
+#define ARC_NOALLOC_MAX_SOURCES 256
+arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, const float* nH,
+                             const float* xHI, const float* xHeI, const float* xHeII, int nsrc,
+                             const double* pos, const double* ndot, float* gamma, float* heat,
+                             double* budget, void* stream);
+
 /* Text of the most recent error on this context (never NULL). */
 const char* arc_last_error(const arc_ctx* ctx);
 

@@ -84,6 +84,9 @@ _SIGS = {
     "arc_stats": ([C.c_void_p, C.POINTER(ArcStats)], C.c_int),
     "arc_set_tuning": ([C.c_void_p, C.c_int, C.c_int, C.c_int], C.c_int),
     "arc_last_error": ([C.c_void_p], C.c_char_p),
+    "arc_trace_noalloc": ([C.POINTER(ArcGrid), C.POINTER(ArcParams)] + [C.c_void_p] * 4 +
+                          [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "arc_destroy": ([C.c_void_p], None),
 }
 
@@ -250,6 +253,34 @@ def arc_stats(ctx) -> dict:
 def arc_set_tuning(ctx, block_threads=0, blocks_per_sm=0, stack_entries=0) -> None:
     _check(ctx, load().arc_set_tuning(C.c_void_p(ctx), int(block_threads), int(blocks_per_sm),
                                       int(stack_entries)))
+
+
+NOALLOC_MAX_N = 64
+NOALLOC_MAX_SOURCES = 256
+
+
+def arc_trace_noalloc(grid: ArcGrid, params: ArcParams, nH, xHI, xHeI, xHeII, pos, ndot, gamma, heat,
+                      stream: Optional[int] = None):
+    """One trace into caller-owned device buffers with no allocation (see
+    include/arc.h).  Fields and outputs are contiguous float32 CUDA tensors;
+    returns the budget[4]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    ndot = np.ascontiguousarray(ndot, dtype=np.float64)
+    ptrs = []
+    for a in (nH, xHI, xHeI, xHeII, gamma, heat):
+        p, on_dev = _ptr_and_kind(a)
+        if not on_dev:
+            raise ValueError("arc_trace_noalloc takes device arrays")
+        ptrs.append(p)
+    b = (C.c_double * 4)()
+    st = load().arc_trace_noalloc(C.byref(grid), C.byref(params), *[C.c_void_p(q) for q in ptrs[:4]],
+                                  pos.shape[0], pos.ctypes.data, ndot.ctypes.data,
+                                  C.c_void_p(ptrs[4]), C.c_void_p(ptrs[5]), b, C.c_void_p(stream or 0))
+    if st != ARC_OK:
+        raise ArcError(st, "arc_trace_noalloc failed (n=%d, %d sources; its fixed scratch allows "
+                       "n <= ARC_NOALLOC_MAX_N=%d, sources <= ARC_NOALLOC_MAX_SOURCES=%d, l_base <= 2)"
+                       % (grid.n, pos.shape[0], NOALLOC_MAX_N, NOALLOC_MAX_SOURCES))
+    return np.array(list(b))
 
 
 def arc_last_error(ctx) -> str:
