@@ -204,6 +204,9 @@ def run_ours(args):
     a = P.Arc(w.n, w.box_cm, p, stream=stream.cuda_stream)
     a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
     a.add_sources(w.src_pos, w.src_ndot)
+    # launch shape chosen by the project's autotuner on the brightest sources
+    a.autotune(max_sources=min(100, w.nsrc), reps=1)
+    tuning = a.get_tuning()
     # the budget of the first trace checks photon conservation at full size
     _, _, budget = a.trace(w.dt_s, budget=True)
     a.chem(w.dt_s)
@@ -237,13 +240,15 @@ def run_ours(args):
 
     # -------- k_trace duration per launch: the same steps run eagerly, CUDA
     # events around each trace launch on the context stream
-    trace_ms, trace_segs = [], []
+    trace_ms, trace_segs, chem_ms, chem_sub = [], [], [], []
     for _ in range(args.steps):
         a.trace(w.dt_s, budget=False)
         a.chem(w.dt_s)
         st = a.stats()
         trace_ms.append(st["trace_ms"])
         trace_segs.append(st["segments"])
+        chem_ms.append(st["chem_ms"])
+        chem_sub.append(st["chem_substeps"])
 
     # -------- end to end through the C ABI with host buffers
     n3 = w.n ** 3
@@ -283,9 +288,14 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (fields 5x64 MB, rates 6x64 MB, "
-                   "accumulators 512 MB per step)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "accumulators 512 MB per step)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "trace_launch": {"block": tuning[0], "blocks_per_sm": tuning[1], "deque_entries": tuning[2],
+                                    "chosen_by": "arc_autotune"}},
         "rt_step_ms": sum(trace_ms) / len(trace_ms), "trace_kernel_ms": trace_ms,
         "segments_per_step": segs / args.steps,
+        "chem_ms": sum(chem_ms) / len(chem_ms),
+        "chem_cells_per_s": w.n ** 3 / (sum(chem_ms) / len(chem_ms) / 1e3),
+        "chem_substeps_per_cell": sum(chem_sub) / len(chem_sub) / w.n ** 3,
         "budget_closure": abs(budget[0] - budget[1] - budget[2]) / budget[0],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,

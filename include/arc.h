@@ -212,6 +212,8 @@ arc_status arc_stats(arc_ctx* ctx, arc_stats_t* out);
  * work-stack entries per warp (power of two, 64..256).  0 keeps a value.
  */
 arc_status arc_set_tuning(arc_ctx* ctx, int block_threads, int blocks_per_sm, int stack_entries);
+/* arc_get_tuning -- the launch shape in use (any pointer may be NULL). */
+arc_status arc_get_tuning(arc_ctx* ctx, int* block_threads, int* blocks_per_sm, int* stack_entries);
 
 /*
  * arc_trace_noalloc -- one radiative-transfer pass, like arc_trace, that
@@ -246,6 +248,18 @@ arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, const float
                              const float* xHI, const float* xHeI, const float* xHeII, int nsrc,
                              const double* pos, const double* ndot, float* gamma, float* heat,
                              double* budget, void* stream);
+
+/*
+ * arc_autotune -- choose the tracer's launch shape for the current fields and
+ * sources by timing it: every candidate (threads per block 128/256, blocks per
+ * SM from the occupancy limit down, deque entries per warp 64/128/256) traces
+ * the brightest `max_sources` sources (0 = all) `reps` times on the context
+ * stream; the fastest shape by CUDA-event time is kept (as arc_set_tuning).
+ * Synchronises.  best_ms (may be NULL) receives the best trace time.
+ * The rates left in the context's buffers afterwards are those of the last
+ * candidate run: call arc_trace again before using them.
+ */
+arc_status arc_autotune(arc_ctx* ctx, int max_sources, int reps, double* best_ms);
 
 /* Text of the most recent error on this context (never NULL). */
 const char* arc_last_error(const arc_ctx* ctx);

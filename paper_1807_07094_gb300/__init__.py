@@ -7,5 +7,6 @@ include/arc.h); ``arc`` is its thin ctypes binding.
 from .arc import (Arc, ArcError, ArcGrid, ArcParams, arc_add_sources, arc_chem_update,  # noqa: F401
                   arc_clear_sources, arc_create, arc_destroy, arc_get_fields,
                   arc_get_record_count, arc_last_error, arc_set_fields, arc_set_records,
-                  arc_set_tuning, arc_stats, arc_step, arc_trace, device_view, load, make_params,
+                  arc_set_tuning, arc_get_tuning, arc_autotune, arc_stats, arc_step, arc_trace,
+                  device_view, load, make_params,
                   REC_DTYPE)

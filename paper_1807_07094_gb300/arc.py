@@ -83,6 +83,8 @@ _SIGS = {
     "arc_get_record_count": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "arc_stats": ([C.c_void_p, C.POINTER(ArcStats)], C.c_int),
     "arc_set_tuning": ([C.c_void_p, C.c_int, C.c_int, C.c_int], C.c_int),
+    "arc_get_tuning": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "arc_autotune": ([C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)], C.c_int),
     "arc_last_error": ([C.c_void_p], C.c_char_p),
     "arc_trace_noalloc": ([C.POINTER(ArcGrid), C.POINTER(ArcParams)] + [C.c_void_p] * 4 +
                           [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -283,6 +285,18 @@ def arc_trace_noalloc(grid: ArcGrid, params: ArcParams, nH, xHI, xHeI, xHeII, po
     return np.array(list(b))
 
 
+def arc_get_tuning(ctx):
+    v = [C.c_int(), C.c_int(), C.c_int()]
+    _check(ctx, load().arc_get_tuning(C.c_void_p(ctx), *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def arc_autotune(ctx, max_sources: int = 0, reps: int = 1) -> float:
+    best = C.c_double()
+    _check(ctx, load().arc_autotune(C.c_void_p(ctx), int(max_sources), int(reps), C.byref(best)))
+    return best.value
+
+
 def arc_last_error(ctx) -> str:
     return load().arc_last_error(C.c_void_p(ctx)).decode()
 
@@ -351,3 +365,9 @@ class Arc:
 
     def set_tuning(self, block_threads=0, blocks_per_sm=0, stack_entries=0):
         arc_set_tuning(self.ctx, block_threads, blocks_per_sm, stack_entries)
+
+    def get_tuning(self):
+        return arc_get_tuning(self.ctx)
+
+    def autotune(self, max_sources: int = 0, reps: int = 1) -> float:
+        return arc_autotune(self.ctx, max_sources, reps)

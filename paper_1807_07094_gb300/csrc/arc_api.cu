@@ -277,7 +277,7 @@ int trace_grid(arc_ctx* c) {
     if (per_sm <= 0) {
         int occ = 0;
         const int smem = trace_smem_bytes(c->block, c->stack_log2);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(), c->block, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(c->p.ngroups), c->block, smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -286,8 +286,10 @@ int trace_grid(arc_ctx* c) {
     return c->num_sms * per_sm;
 }
 
-// queue the trace of the current fields on the context stream (no sync)
-arc_status enqueue_trace(arc_ctx* c) {
+// queue the trace of the current fields on the context stream (no sync);
+// seeds_limit > 0 traces only the first seeds_limit emitted items (the
+// brightest sources), used by the autotuner
+arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
     PrepArgs P;
     memset(&P, 0, sizeof P);
     P.n = c->n;
@@ -305,9 +307,10 @@ arc_status enqueue_trace(arc_ctx* c) {
     P.acc = c->acc;
     CK(launch_prep(P, c->stream));
     TraceArgs A = trace_args(c);
-    CK(launch_seed_reset(A, c->qcap, c->nseeds, c->stream));
+    if (seeds_limit > 0 && seeds_limit < A.nseeds) A.nseeds = seeds_limit;
+    CK(launch_seed_reset(A, c->qcap, A.nseeds, c->stream));
     CK(record_event(c, c->ev[0]));
-    if (c->nseeds > 0) CK(launch_trace(A, trace_grid(c), c->block, c->stream));
+    if (A.nseeds > 0) CK(launch_trace(A, trace_grid(c), c->block, c->stream));
     CK(record_event(c, c->ev[1]));
     FinalizeArgs F;
     memset(&F, 0, sizeof F);
@@ -400,9 +403,10 @@ arc_status arc_create(arc_ctx** out, const arc_grid* g, const arc_params* p, voi
         c->own_stream = true;
     }
     // allow the largest tuning (256 threads x 256 deque entries) once, for every context
-    if (cudaFuncSetAttribute(trace_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             trace_smem_bytes(256, 8)) != cudaSuccess)
-        return bail(ARC_E_CUDA);
+    for (int ng : {1, 3, 4})
+        if (cudaFuncSetAttribute(trace_kernel_ptr(ng), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 trace_smem_bytes(256, 8)) != cudaSuccess)
+            return bail(ARC_E_CUDA);
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(ARC_E_CUDA);
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return bail(ARC_E_CUDA);
@@ -617,6 +621,14 @@ arc_status arc_stats(arc_ctx* c, arc_stats_t* out) {
     return ARC_OK;
 }
 
+arc_status arc_get_tuning(arc_ctx* c, int* block_threads, int* blocks_per_sm, int* stack_entries) {
+    if (!c) return ARC_E_INVALID;
+    if (block_threads) *block_threads = c->block;
+    if (blocks_per_sm) *blocks_per_sm = c->blocks_per_sm > 0 ? c->blocks_per_sm : trace_grid(c) / c->num_sms;
+    if (stack_entries) *stack_entries = 1 << c->stack_log2;
+    return ARC_OK;
+}
+
 arc_status arc_set_tuning(arc_ctx* c, int block_threads, int blocks_per_sm, int stack_entries) {
     if (!c) return ARC_E_INVALID;
     if (block_threads) {
@@ -634,6 +646,67 @@ arc_status arc_set_tuning(arc_ctx* c, int block_threads, int blocks_per_sm, int 
         c->stack_log2 = lg;
     }
     c->graph_valid = false;
+    return ARC_OK;
+}
+
+arc_status arc_autotune(arc_ctx* c, int max_sources, int reps, double* best_ms) {
+    if (!c) return ARC_E_INVALID;
+    if (!c->fields_set) return fail(c, ARC_E_STATE, "arc_set_fields must come first");
+    if (reps < 1 || reps > 16) return fail(c, ARC_E_INVALID, "reps outside 1..16");
+    arc_status st = upload_sources(c);
+    if (st != ARC_OK) return st;
+    const int per_src = 3 << (2 * c->p.l_base);
+    const int limit = (max_sources > 0) ? max_sources * per_src : 0;
+    const int blocks[2] = {128, 256};
+    const int stacks[3] = {6, 7, 8};
+    const int save_block = c->block, save_bps = c->blocks_per_sm, save_stack = c->stack_log2;
+    double best = 1e300;
+    int bb = save_block, bbps = save_bps, bst = save_stack;
+    for (int bi = 0; bi < 2; ++bi)
+        for (int si = 0; si < 3; ++si) {
+            int occ = 0;
+            const int smem = trace_smem_bytes(blocks[bi], stacks[si]);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(c->p.ngroups), blocks[bi],
+                                                              smem) != cudaSuccess || occ < 1)
+                continue;
+            for (int bps = occ; bps >= 1 && bps >= occ - 1; --bps) {
+                c->block = blocks[bi];
+                c->blocks_per_sm = bps;
+                c->stack_log2 = stacks[si];
+                double tot = 0.0;
+                for (int r = 0; r < reps; ++r) {
+                    st = enqueue_trace(c, limit);
+                    if (st != ARC_OK) break;
+                    CK(cudaStreamSynchronize(c->stream));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+                    tot += ms;
+                }
+                if (st != ARC_OK) break;
+                Scalars S;
+                st = sync_status(c, &S);
+                if (st == ARC_OK) st = status_to_error(c, S.status);
+                if (st != ARC_OK) break;
+                if (tot / reps < best) {
+                    best = tot / reps;
+                    bb = c->block;
+                    bbps = bps;
+                    bst = c->stack_log2;
+                }
+            }
+            if (st != ARC_OK) break;
+        }
+    if (st != ARC_OK) {
+        c->block = save_block;
+        c->blocks_per_sm = save_bps;
+        c->stack_log2 = save_stack;
+        return st;
+    }
+    c->block = bb;
+    c->blocks_per_sm = bbps;
+    c->stack_log2 = bst;
+    c->graph_valid = false;
+    if (best_ms) *best_ms = best;
     return ARC_OK;
 }
 

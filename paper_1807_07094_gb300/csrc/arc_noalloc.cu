@@ -221,8 +221,8 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
         NA_CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev));
         const int block = 256;
         const int smem = trace_smem_bytes(block, A.stack_log2);
-        NA_CK(cudaFuncSetAttribute(trace_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(), block, smem) != cudaSuccess ||
+        NA_CK(cudaFuncSetAttribute(trace_kernel_ptr(G), cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(G), block, smem) != cudaSuccess ||
             occ < 1)
             occ = 1;
         NA_CK(launch_trace(A, dev_sms * occ, block, s));

@@ -79,14 +79,12 @@ __device__ __forceinline__ float4 atom_add_v4(float4* a, float4 v) {
     float4 o;
     asm volatile("atom.global.add.v4.f32 {%0,%1,%2,%3}, [%4], {%5,%6,%7,%8};"
                  : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
-                 : "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
+                 : "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
     return o;
 }
 __device__ __forceinline__ void red_add_v4(float4* a, float4 v) {
     asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(a), "f"(v.x), "f"(v.y),
-                 "f"(v.z), "f"(v.w)
-                 : "memory");
+                 "f"(v.z), "f"(v.w));
 }
 __device__ __forceinline__ float4 ldg_f4(const float4* p) { return __ldg(p); }
 
@@ -307,6 +305,8 @@ struct Ray {
     float r, rstop, thr;
     float4 N;              // photons per group (high part)
     float4 Nl;             // low part: the photons are N + Nl
+    float4 kap;            // optical depth per cell length of the current cell
+    uint64_t idx;          // internal index of the current cell
     uint64_t pix;
     uint32_t src;
     int level;
@@ -347,25 +347,33 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
     R.tx = (u.x != 0.0f) ? next_plane_t(R.cx, R.ox, R.ix) : INFINITY;
     R.ty = (u.y != 0.0f) ? next_plane_t(R.cy, R.oy, R.iy) : INFINITY;
     R.tz = (u.z != 0.0f) ? next_plane_t(R.cz, R.oz, R.iz) : INFINITY;
+    R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
+    R.kap = ldg_f4(&A.kappa[R.idx]);
     return EV_NONE;
 }
 
 // One cell segment (Sec. 2.4): to the nearest X/Y/Z boundary or the split
-// distance, Eq. (ion) absorption in every group, deposit, then step.
+// distance, Eq. (ion) absorption in each of the NG groups, then step.  The
+// next cell's record is loaded before the current cell's deposit is issued, so
+// the load and the atomic round trip overlap.
+template <int NG>
 __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
     const float t = fminf(R.tx, fminf(R.ty, R.tz));
     const bool split = R.rstop <= t;
     const float r1 = split ? R.rstop : t;
     const float ds = fmaxf(r1 - R.r, 0.0f);
-    const uint64_t idx = brick_index(R.cx, R.cy, R.cz, A.nb);
-    const float4 kap = ldg_f4(&A.kappa[idx]);
+    const uint64_t idx = R.idx;
+    const float4 kap = R.kap;
     const float4 Nh0 = R.N, Nl0 = R.Nl;
-    float4 D, E;
+    float4 D = make_float4(0.f, 0.f, 0.f, 0.f), E = make_float4(0.f, 0.f, 0.f, 0.f);
     absorb(R.N.x, R.Nl.x, kap.x * ds, D.x, E.x);
-    absorb(R.N.y, R.Nl.y, kap.y * ds, D.y, E.y);
-    absorb(R.N.z, R.Nl.z, kap.z * ds, D.z, E.z);
-    absorb(R.N.w, R.Nl.w, kap.w * ds, D.w, E.w);
-    const float sumN = R.N.x + R.N.y + R.N.z + R.N.w;
+    if (NG > 1) absorb(R.N.y, R.Nl.y, kap.y * ds, D.y, E.y);
+    if (NG > 2) absorb(R.N.z, R.Nl.z, kap.z * ds, D.z, E.z);
+    if (NG > 3) absorb(R.N.w, R.Nl.w, kap.w * ds, D.w, E.w);
+    float sumN = R.N.x;
+    if (NG > 1) sumN += R.N.y;
+    if (NG > 2) sumN += R.N.z;
+    if (NG > 3) sumN += R.N.w;
     const bool term = sumN < R.thr;
     if (term) {
         // below threshold: every remaining photon stays in this cell
@@ -374,35 +382,48 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
         R.N = make_float4(0.f, 0.f, 0.f, 0.f);
         R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    R.visits++;
+    R.r = r1;
+    int ev = term ? EV_TERM : (split ? EV_SPLIT : EV_NONE);
+    if (ev == EV_NONE) {
+        // step across the nearest face; ties go to the lowest axis (x, y, z)
+        const int n = A.n;
+        bool out;
+        if (R.tx <= R.ty && R.tx <= R.tz) {
+            R.cx += (R.ix > 0.f) ? 1 : -1;
+            out = R.cx < 0 || R.cx >= n;
+            if (!out) R.tx = next_plane_t(R.cx, R.ox, R.ix);
+        } else if (R.ty <= R.tz) {
+            R.cy += (R.iy > 0.f) ? 1 : -1;
+            out = R.cy < 0 || R.cy >= n;
+            if (!out) R.ty = next_plane_t(R.cy, R.oy, R.iy);
+        } else {
+            R.cz += (R.iz > 0.f) ? 1 : -1;
+            out = R.cz < 0 || R.cz >= n;
+            if (!out) R.tz = next_plane_t(R.cz, R.oz, R.iz);
+        }
+        if (out) {
+            ev = EV_ESC;
+        } else {
+            R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
+            R.kap = ldg_f4(&A.kappa[R.idx]);
+        }
+    }
     if (D.x != 0.f || D.y != 0.f || D.z != 0.f || D.w != 0.f || E.x != 0.f || E.y != 0.f ||
         E.z != 0.f || E.w != 0.f)
         deposit(A.acc, idx, D, E);
-    R.visits++;
-    R.r = r1;
-    if (term) return EV_TERM;
-    if (split) return EV_SPLIT;
-    // step across the nearest face; ties go to the lowest axis (x, y, z)
-    const int n = A.n;
-    if (R.tx <= R.ty && R.tx <= R.tz) {
-        R.cx += (R.ix > 0.f) ? 1 : -1;
-        if (R.cx < 0 || R.cx >= n) return EV_ESC;
-        R.tx = next_plane_t(R.cx, R.ox, R.ix);
-    } else if (R.ty <= R.tz) {
-        R.cy += (R.iy > 0.f) ? 1 : -1;
-        if (R.cy < 0 || R.cy >= n) return EV_ESC;
-        R.ty = next_plane_t(R.cy, R.oy, R.iy);
-    } else {
-        R.cz += (R.iz > 0.f) ? 1 : -1;
-        if (R.cz < 0 || R.cz >= n) return EV_ESC;
-        R.tz = next_plane_t(R.cz, R.oz, R.iz);
-    }
-    return EV_NONE;
+    return ev;
 }
 
 constexpr int SEG_BATCH = 4;          // segments per lane between warp event rounds
 constexpr int HEARTBEAT_EVERY = 1024; // event rounds between progress signals
 
-__global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
+#ifndef ARC_TRACE_MIN_BLOCKS
+#define ARC_TRACE_MIN_BLOCKS 2   // resident 256-thread blocks per SM the registers must allow
+                                 // (2: no spills; measured faster than 3 or 4 with spills)
+#endif
+template <int NG>
+__global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -414,7 +435,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
     // deque [bot, top) of pending work items, indices modulo cap (warp-uniform)
     unsigned bot = 0, top = 0;
     long long live_delta = 0;          // lane 0 only: rays created minus finished, not yet flushed
-    unsigned long long nseg = 0, nrays = 0, nsplit = 0, nterm = 0, nesc = 0, ndon = 0;
+    unsigned nseg = 0, nrays = 0, nsplit = 0, nterm = 0, nesc = 0, ndon = 0;   // per lane
     unsigned maxlev = 0;
     double esc_photons = 0.0;
     unsigned round = 0;
@@ -564,7 +585,7 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
         if (active && ev == EV_NONE) {
 #pragma unroll 1
             for (int it = 0; it < SEG_BATCH; ++it) {
-                ev = segment(A, R);
+                ev = segment<NG>(A, R);
                 nseg++;
                 if (ev != EV_NONE) break;
             }
@@ -627,7 +648,8 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
                     e.key = make_key(R.pix << 2, R.level + 1, 1);
                     e.src = R.src;
                     e.r = R.r;
-                    e.N = make_float4(R.N.x * 0.25f, R.N.y * 0.25f, R.N.z * 0.25f, R.N.w * 0.25f);
+                    e.N = make_float4(R.N.x * 0.25f, NG > 1 ? R.N.y * 0.25f : 0.f,
+                                      NG > 2 ? R.N.z * 0.25f : 0.f, NG > 3 ? R.N.w * 0.25f : 0.f);
                     if (room) stack[(top + __popc(sm & lt_mask)) & cmask] = e;
                     nsplit++;
                     // children 1..3 carry exact FP32 quarters; child 0 (this lane)
@@ -670,8 +692,11 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
 
     // ------------------------------------------------------------ totals
     flush_live();
+    // per-lane counts stay far below 2^32 per launch; warp sums are formed in
+    // the 64-bit atomics below, lane by lane
+    unsigned long long wseg = nseg;
     for (int o = 16; o > 0; o >>= 1) {
-        nseg += __shfl_down_sync(FULL, nseg, o);
+        wseg += __shfl_down_sync(FULL, wseg, o);
         nrays += __shfl_down_sync(FULL, nrays, o);
         nsplit += __shfl_down_sync(FULL, nsplit, o);
         nterm += __shfl_down_sync(FULL, nterm, o);
@@ -680,13 +705,13 @@ __global__ void __launch_bounds__(256, 3) k_trace(const TraceArgs A) {
         maxlev = max(maxlev, __shfl_down_sync(FULL, maxlev, o));
     }
     if (lane == 0) {
-        atomicAdd(&A.counters[CNT_SEG], nseg);
-        atomicAdd(&A.counters[CNT_SEG_TOTAL], nseg);
-        atomicAdd(&A.counters[CNT_RAYS], nrays);
-        atomicAdd(&A.counters[CNT_SPLIT], nsplit);
-        atomicAdd(&A.counters[CNT_TERM], nterm);
-        atomicAdd(&A.counters[CNT_ESC], nesc);
-        atomicAdd(&A.counters[CNT_DONATE], ndon);
+        atomicAdd(&A.counters[CNT_SEG], wseg);
+        atomicAdd(&A.counters[CNT_SEG_TOTAL], wseg);
+        atomicAdd(&A.counters[CNT_RAYS], (unsigned long long)nrays);
+        atomicAdd(&A.counters[CNT_SPLIT], (unsigned long long)nsplit);
+        atomicAdd(&A.counters[CNT_TERM], (unsigned long long)nterm);
+        atomicAdd(&A.counters[CNT_ESC], (unsigned long long)nesc);
+        atomicAdd(&A.counters[CNT_DONATE], (unsigned long long)ndon);
         atomicMax(&A.counters[CNT_MAXLEVEL], (unsigned long long)maxlev);
         if (esc_photons != 0.0) atomicAdd(A.escaped, esc_photons);
     }
@@ -844,7 +869,12 @@ __global__ void k_budget(const double* part, int nparts, const double* escaped, 
 int trace_smem_bytes(int block, int stack_log2) {
     return (block / 32) * (1 << stack_log2) * (int)sizeof(Entry);
 }
-const void* trace_kernel_ptr() { return (const void*)k_trace; }
+// the tracer is specialised on the number of frequency groups carried
+const void* trace_kernel_ptr(int ng) {
+    if (ng <= 1) return (const void*)k_trace<1>;
+    if (ng <= 3) return (const void*)k_trace<3>;
+    return (const void*)k_trace<4>;
+}
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
     k_prep<<<152 * 8, 256, 0, s>>>(a);
@@ -872,7 +902,9 @@ cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int n
 }
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s) {
     const int smem = trace_smem_bytes(block, a.stack_log2);
-    k_trace<<<grid, block, smem, s>>>(a);
+    if (a.ng <= 1) k_trace<1><<<grid, block, smem, s>>>(a);
+    else if (a.ng <= 3) k_trace<3><<<grid, block, smem, s>>>(a);
+    else k_trace<4><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s) {

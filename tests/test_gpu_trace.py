@@ -159,3 +159,25 @@ def test_full_size_cosmic_256_sampled_sources(src):
     both sides (the whole 1000-source step is out of the oracle's reach)."""
     w = W.subset_sources(W.cosmic_256(), src)
     check_pair(w, records=True)
+
+
+def test_autotune_picks_a_shape_and_keeps_results():
+    """The autotuner times candidate launch shapes and keeps the fastest; the
+    traced result does not depend on the shape it picked."""
+    import paper_1807_07094_gb300 as P
+    w = W.cosmic(n=64, nsrc=24, sigma_ln=1.5, seed=12)
+    xs = partly_ionised(w, seed=5, lo=-4, hi=0)
+    ref = gpu_trace(w, *xs)
+    with P.Arc(w.n, w.box_cm, w.params()) as a:
+        a.set_fields(w.nH, xs[0], xs[1], xs[2], w.T)
+        a.add_sources(w.src_pos, w.src_ndot)
+        best = a.autotune(max_sources=8, reps=1)
+        assert best > 0
+        block, bps, stack = a.get_tuning()
+        assert block in (128, 256) and stack in (64, 128, 256) and bps >= 1
+        g, h, b = a.trace(1.0, budget=True)
+        g = g.cpu().numpy().astype(np.float64)
+    for s in range(3):
+        o = ref["gamma"][s]
+        m = o > 1e-6 * o.max()
+        assert np.max(np.abs(g[s][m] / o[m] - 1)) < 1e-5
