@@ -186,6 +186,39 @@ def run_reference(args):
     return 0
 
 
+def surrogate_speedup(a, w, P, reps: int = 3):
+    """Chemistry cells/s of the surrogate path against the plain solver, both
+    on the current state with rates from a fresh trace (CUDA events around
+    each chemistry update on the context stream)."""
+    a.trace(w.dt_s, budget=False)
+    state = a.get_fields()
+    params, norm, meta = P.load_surrogate()
+    res = {}
+    for arm in ("plain", "surrogate"):
+        if arm == "surrogate":
+            a.set_surrogate(params, norm)
+        ms, st = [], None
+        for _ in range(reps):
+            a.set_fields(w.nH, *state)
+            a.chem(w.dt_s)
+            st = a.stats()
+            ms.append(st["chem_ms"])
+        res[arm] = dict(ms=ms, out=a.get_fields(), stats=st)
+    a.set_surrogate(None)
+    a.set_fields(w.nH, *state)
+    n3 = w.n ** 3
+    t_plain = sorted(res["plain"]["ms"])[reps // 2]
+    t_surr = sorted(res["surrogate"]["ms"])[reps // 2]
+    u, v = res["plain"]["out"], res["surrogate"]["out"]
+    return {"plain_cells_per_s": n3 / (t_plain / 1e3), "surrogate_cells_per_s": n3 / (t_surr / 1e3),
+            "speedup": t_plain / t_surr, "plain_ms": res["plain"]["ms"], "surrogate_ms": res["surrogate"]["ms"],
+            "accepted_frac": res["surrogate"]["stats"]["surrogate_cells"] / n3,
+            "plain_substeps_per_cell": res["plain"]["stats"]["chem_substeps"] / n3,
+            "max_dx_vs_plain": float(max(np.abs(x - y).max() for x, y in zip(u[:3], v[:3]))),
+            "max_dT_rel_vs_plain": float(np.abs(v[3] / u[3] - 1).max()),
+            "weights": {"file": os.path.basename(P.SURROGATE_FILE), "samples": meta.get("samples")}}
+
+
 def run_ours(args):
     import torch
     import paper_1807_07094_gb300 as P
@@ -250,6 +283,12 @@ def run_ours(args):
         chem_ms.append(st["chem_ms"])
         chem_sub.append(st["chem_substeps"])
 
+    # -------- chemistry: learned surrogate (network + residual check + plain
+    # fallback) against the plain sub-cycled solver on the same state and rates
+    surrogate = None
+    if not args.no_surrogate and os.path.exists(P.SURROGATE_FILE):
+        surrogate = surrogate_speedup(a, w, P)
+
     # -------- end to end through the C ABI with host buffers
     n3 = w.n ** 3
     pinned = [torch.empty(n3, dtype=torch.float32).pin_memory() for _ in range(5)]
@@ -304,6 +343,7 @@ def run_ours(args):
                      "kernel": "k_trace", "algo_bytes_per_segment": ALGO_BYTES_PER_SEGMENT},
         "e2e": {"value": segs_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * 4 * n3,
                 "d2h_bytes_per_step": 4 * 4 * n3},
+        "surrogate": surrogate,
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
     }
@@ -324,6 +364,7 @@ def main():
     ap.add_argument("--sources", type=int, default=1000,
                     help="profiling aid: trace only the first N sources of the workload")
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the e2e pass")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-ODE chemistry comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

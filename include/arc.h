@@ -104,6 +104,8 @@ typedef struct {
     double chem_ms;          /* device time of the last chemistry update              */
     uint64_t segments_total; /* segments summed over every trace of this context      */
     uint64_t traces_total;   /* traces run by this context                            */
+    uint64_t surrogate_cells;/* cells updated by the surrogate in the last chemistry  */
+    uint64_t fallback_cells; /* cells the residual check sent to the plain solver     */
 } arc_stats_t;
 
 /* One record per ray (test aid, see arc_set_records). */
@@ -260,6 +262,73 @@ arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, const float
  * candidate run: call arc_trace again before using them.
  */
 arc_status arc_autotune(arc_ctx* ctx, int max_sources, int reps, double* best_ms);
+
+/* ------------------------------------------------------------------------
+ * Chemistry surrogate (a learned stand-in for the sub-cycled update of
+ * arc_chem_update; the paper has none).  Per cell an MLP
+ * 12 -> 64 -> 64 -> 64 -> 4 with SiLU maps
+ *   features  log10 nH, x_HI, x_HeI, x_HeII, log10 T, log10(Gamma_s + 1e-30) x3,
+ *             log10(H_s + 1e-40) x3, log10 dt
+ * to the step's changes r = (x_HI' - x_HI, x_HeI' - x_HeI, x_HeII' - x_HeII,
+ * log10(T'/T)).  Inputs are normalised as (v - mu) / sd; the network's k-th
+ * output o_k stands for r_k = s_k sinh(o_k sd_k + mu_k), so that small and
+ * large changes are resolved alike.
+ * Parameters: ARC_MLP_NPARAMS FP32 values in the order
+ *   W1[64][12], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[4][64], b4[4];
+ * normalisation: 36 FP32 values  in_mu[12], in_sd[12], out_mu[4], out_sd[4],
+ * out_s[4] (all sd and s > 0).
+ * Products run on the tensor cores with BF16 operands and FP32 accumulation.
+ * ------------------------------------------------------------------------ */
+#define ARC_MLP_NPARAMS 9412
+#define ARC_MLP_NNORM 36
+
+/*
+ * arc_set_surrogate -- load surrogate parameters (host arrays) into the
+ * context and use them in arc_chem_update / arc_step: every cell takes the
+ * network's step unless a residual check rejects it -- the frozen-coefficient
+ * solutions of Eq. (anninos) from the start state and from the predicted end
+ * state must agree within tol_x (neutral fraction) and bracket the prediction,
+ * and the start and end heating-minus-cooling rates must agree with the
+ * predicted energy change within tol_e (relative) -- in which case the plain
+ * sub-cycled solver updates that cell.  params = NULL switches the surrogate
+ * off.  Synchronises.
+ */
+arc_status arc_set_surrogate(arc_ctx* ctx, const float* params, const float* norm, double tol_x, double tol_e);
+
+/* Training.  A trainer holds FP32 master weights, AdamW moments and the
+ * activations of one batch of up to max_batch samples (a multiple of 16). */
+typedef struct arc_mlp_trainer arc_mlp_trainer;
+arc_status arc_mlp_trainer_create(arc_mlp_trainer** out, int max_batch, void* stream);
+/* copy in parameters (host, ARC_MLP_NPARAMS) and reset the AdamW state */
+arc_status arc_mlp_trainer_set_params(arc_mlp_trainer* t, const float* params);
+arc_status arc_mlp_trainer_get_params(arc_mlp_trainer* t, float* params);
+/* Gradient of the mean-squared error over n samples (n % 16 == 0, n <= max_batch).
+ * X: device n x 12 normalised features; Y: device n x 4 normalised targets
+ * ((asinh(r_k / s_k) - mu_k) / sd_k);
+ * grad (host ARC_MLP_NPARAMS, may be NULL) and loss (host, may be NULL) receive
+ * the result.  Synchronises. */
+arc_status arc_mlp_grad(arc_mlp_trainer* t, const float* X, const float* Y, int n, float* grad, double* loss);
+/* One AdamW step (beta1 0.9, beta2 0.999, decoupled weight decay wd on the
+ * matrices).  loss (may be NULL) receives the batch loss before the step and
+ * then the call synchronises; with loss = NULL it is asynchronous. */
+arc_status arc_mlp_train_step(arc_mlp_trainer* t, const float* X, const float* Y, int n, double lr, double wd,
+                              double* loss);
+void arc_mlp_trainer_destroy(arc_mlp_trainer* t);
+/* Inference kernel of arc_chem_update's surrogate on given raw features:
+ * X device n x 12 (unnormalised), Y device n x 4 (the changes r_k).
+ * Allocates its own weight buffers; synchronises. */
+arc_status arc_mlp_eval(const float* params, const float* norm, const float* X, long long n, float* Y,
+                        void* stream);
+
+/* Surrogate features of n cells (device arrays of n FP32; gamma, heat 3 x n
+ * species-major) -> X device n x 12, as the inference kernel forms them. */
+arc_status arc_mlp_features(const float* nH, const float* xHI, const float* xHeI, const float* xHeII,
+                            const float* T, const float* gamma, const float* heat, double dt, long long n, float* X,
+                            void* stream);
+/* Surrogate targets from the states before (x0: 3 x n, T0) and after (x1, T1)
+ * a chemistry step -> Y device n x 4. */
+arc_status arc_mlp_targets(const float* x0, const float* x1, const float* T0, const float* T1, long long n, float* Y,
+                           void* stream);
 
 /* Text of the most recent error on this context (never NULL). */
 const char* arc_last_error(const arc_ctx* ctx);

@@ -112,6 +112,9 @@ def lib(path: Optional[str] = None):
         L.orc_chem.argtypes = [C.POINTER(OrcParams), C.c_int64, dp, dp, dp, dp, dp, dp, dp,
                                C.c_double, C.POINTER(C.c_int64)]
         L.orc_chem.restype = C.c_int
+        L.orc_chem_refined.argtypes = [C.POINTER(OrcParams), C.c_int64, dp, dp, dp, dp, dp, dp, dp,
+                                       C.c_double, C.c_int, C.POINTER(C.c_int64)]
+        L.orc_chem_refined.restype = C.c_int
         L.orc_rates.argtypes = [C.POINTER(OrcParams), C.c_double, dp]
         L.orc_cooling.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double, C.c_double]
@@ -187,8 +190,9 @@ def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool =
                 recs=recs[: nrec.value] if records else None)
 
 
-def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float):
-    """Chemistry over dt; returns (xHI, xHeI, xHeII, T, nsub, capped) as float64."""
+def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float, min_sub: int = 0):
+    """Chemistry over dt; returns (xHI, xHeI, xHeII, T, nsub, capped) as float64.
+    min_sub > 0 also caps every sub-step at dt / min_sub (orc_chem_refined)."""
     p = make_params(params)
     f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1)).copy()
     nH = f(nH)
@@ -198,8 +202,12 @@ def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float):
     ncell = nH.size
     assert g.size == 3 * ncell and h.size == 3 * ncell
     nsub = C.c_int64(0)
-    capped = lib().orc_chem(C.byref(p), ncell, _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII),
-                            _dptr(T), _dptr(g), _dptr(h), float(dt), C.byref(nsub))
+    if min_sub > 0:
+        capped = lib().orc_chem_refined(C.byref(p), ncell, _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII),
+                                        _dptr(T), _dptr(g), _dptr(h), float(dt), int(min_sub), C.byref(nsub))
+    else:
+        capped = lib().orc_chem(C.byref(p), ncell, _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII),
+                                _dptr(T), _dptr(g), _dptr(h), float(dt), C.byref(nsub))
     return xHI, xHeI, xHeII, T, int(nsub.value), int(capped)
 
 

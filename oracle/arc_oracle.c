@@ -454,9 +454,13 @@ double orc_cooling(const orc_params* p, double T, double nH, double nHI, double 
     return L;
 }
 
-int orc_chem(const orc_params* p, int64_t ncell, const double* nHa,
-             double* xHI, double* xHeI, double* xHeII, double* Ta,
-             const double* gamma, const double* heat, double dt, int64_t* nsub_out) {
+/* The sub-cycled update; min_sub > 0 also caps every sub-step at dt / min_sub
+ * (a uniform refinement under which all species converge as min_sub grows;
+ * the paper's limiter, min_sub = 0, controls only n_HI, n_HII and E). */
+static int chem_subcycled(const orc_params* p, int64_t ncell, const double* nHa,
+                          double* xHI, double* xHeI, double* xHeII, double* Ta,
+                          const double* gamma, const double* heat, double dt, int min_sub,
+                          int64_t* nsub_out) {
     const double y = p->Y / (4.0 * (1.0 - p->Y));
     const double eps = p->eps_sub;
     int capped = 0;
@@ -487,6 +491,10 @@ int orc_chem(const orc_params* p, int64_t ncell, const double* nHa,
              * n_HII (the hydrogen densities floored at x_fp64 n_H) */
             double h = dt - t;
             int last = 1;
+            if (min_sub > 0 && h > dt / min_sub) {
+                h = dt / min_sub;
+                last = 0;
+            }
             const double lim = eps * fmax(fmin(nHI, nH - nHI), p->x_fp64 * nH);
             if (fabs(dnHI) * h > lim) {
                 h = lim / fabs(dnHI);
@@ -531,4 +539,18 @@ int orc_chem(const orc_params* p, int64_t ncell, const double* nHa,
     }
     if (nsub_out) *nsub_out = nsub_total;
     return capped;
+}
+
+int orc_chem(const orc_params* p, int64_t ncell, const double* nHa,
+             double* xHI, double* xHeI, double* xHeII, double* Ta,
+             const double* gamma, const double* heat, double dt, int64_t* nsub_out) {
+    return chem_subcycled(p, ncell, nHa, xHI, xHeI, xHeII, Ta, gamma, heat, dt, 0, nsub_out);
+}
+
+int orc_chem_refined(const orc_params* p, int64_t ncell, const double* nHa,
+                     double* xHI, double* xHeI, double* xHeII, double* Ta,
+                     const double* gamma, const double* heat, double dt, int min_sub,
+                     int64_t* nsub_out) {
+    if (min_sub < 1) return -1;
+    return chem_subcycled(p, ncell, nHa, xHI, xHeI, xHeII, Ta, gamma, heat, dt, min_sub, nsub_out);
 }

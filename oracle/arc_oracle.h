@@ -99,6 +99,16 @@ int orc_chem(const orc_params* p, int64_t ncell, const double* nH,
              double* xHI, double* xHeI, double* xHeII, double* T,
              const double* gamma, const double* heat, double dt, int64_t* nsub);
 
+/* The same update with every sub-step also capped at dt / min_sub (min_sub
+ * >= 1, else -1): a uniform refinement under which all species converge to
+ * the solution of the rate equations as min_sub grows.  The paper's limiter
+ * bounds only the changes of n_HI, n_HII and E per sub-step, so the helium
+ * fractions of orc_chem carry the first-order error of the step it takes. */
+int orc_chem_refined(const orc_params* p, int64_t ncell, const double* nH,
+                     double* xHI, double* xHeI, double* xHeII, double* T,
+                     const double* gamma, const double* heat, double dt, int min_sub,
+                     int64_t* nsub);
+
 /* Rate coefficients at temperature T (for tests):
  * out[0..5] = alpha_HII, alpha_HeII(+dielectronic), alpha_HeIII,
  *             beta_HI, beta_HeI, beta_HeII  [cm^3/s]. */

@@ -11,6 +11,7 @@ arc_trace, arc_chem_update, arc_step, arc_get_fields, arc_stats, ...).
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
 from typing import Optional
 
@@ -55,7 +56,7 @@ class ArcStats(C.Structure):
         ("max_level", C.c_uint32), ("error_word", C.c_uint32), ("chem_substeps", C.c_uint64),
         ("chem_fp64_substeps", C.c_uint64), ("chem_capped", C.c_uint64),
         ("trace_ms", C.c_double), ("chem_ms", C.c_double), ("segments_total", C.c_uint64),
-        ("traces_total", C.c_uint64),
+        ("traces_total", C.c_uint64), ("surrogate_cells", C.c_uint64), ("fallback_cells", C.c_uint64),
     ]
 
     def as_dict(self):
@@ -90,7 +91,21 @@ _SIGS = {
                           [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "arc_destroy": ([C.c_void_p], None),
+    "arc_set_surrogate": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double], C.c_int),
+    "arc_mlp_trainer_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p], C.c_int),
+    "arc_mlp_trainer_set_params": ([C.c_void_p, C.c_void_p], C.c_int),
+    "arc_mlp_trainer_get_params": ([C.c_void_p, C.c_void_p], C.c_int),
+    "arc_mlp_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double)], C.c_int),
+    "arc_mlp_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                            C.POINTER(C.c_double)], C.c_int),
+    "arc_mlp_trainer_destroy": ([C.c_void_p], None),
+    "arc_mlp_eval": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
+    "arc_mlp_features": ([C.c_void_p] * 7 + [C.c_double, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
+    "arc_mlp_targets": ([C.c_void_p] * 4 + [C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
 }
+
+MLP_NPARAMS = 9412
+MLP_NNORM = 36
 
 
 def lib_path() -> str:
@@ -297,6 +312,113 @@ def arc_autotune(ctx, max_sources: int = 0, reps: int = 1) -> float:
     return best.value
 
 
+def _f32_host(a, size):
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    if a.size != size:
+        raise ValueError(f"expected {size} float32 values, got {a.size}")
+    return a
+
+
+def _dev(a):
+    p, on_dev = _ptr_and_kind(a)
+    if not on_dev:
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return p
+
+
+def arc_set_surrogate(ctx, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2) -> None:
+    if params is None:
+        _check(ctx, load().arc_set_surrogate(C.c_void_p(ctx), None, None, 0.0, 0.0))
+        return
+    p = _f32_host(params, MLP_NPARAMS)
+    q = _f32_host(norm, MLP_NNORM)
+    _check(ctx, load().arc_set_surrogate(C.c_void_p(ctx), p.ctypes.data, q.ctypes.data, float(tol_x), float(tol_e)))
+
+
+def _mlp_check(st, what):
+    if st != ARC_OK:
+        raise ArcError(st, what)
+
+
+class MlpTrainer:
+    """GPU trainer of the chemistry surrogate (BF16 tensor-core forward and
+    backward passes, FP32 AdamW)."""
+
+    def __init__(self, max_batch: int, stream: Optional[int] = None):
+        h = C.c_void_p()
+        _mlp_check(load().arc_mlp_trainer_create(C.byref(h), int(max_batch), C.c_void_p(stream or 0)),
+                   "arc_mlp_trainer_create")
+        self.h = h.value
+
+    def close(self):
+        if self.h:
+            load().arc_mlp_trainer_destroy(C.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = _f32_host(params, MLP_NPARAMS)
+        _mlp_check(load().arc_mlp_trainer_set_params(C.c_void_p(self.h), p.ctypes.data), "set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(MLP_NPARAMS, np.float32)
+        _mlp_check(load().arc_mlp_trainer_get_params(C.c_void_p(self.h), p.ctypes.data), "get_params")
+        return p
+
+    def grad(self, X, Y, n: int):
+        g = np.empty(MLP_NPARAMS, np.float32)
+        loss = C.c_double()
+        _mlp_check(load().arc_mlp_grad(C.c_void_p(self.h), C.c_void_p(_dev(X)), C.c_void_p(_dev(Y)), int(n),
+                                       g.ctypes.data, C.byref(loss)), "arc_mlp_grad")
+        return g, loss.value
+
+    def step(self, X, Y, n: int, lr: float, wd: float = 0.0, want_loss: bool = False):
+        loss = C.c_double()
+        _mlp_check(load().arc_mlp_train_step(C.c_void_p(self.h), C.c_void_p(_dev(X)), C.c_void_p(_dev(Y)), int(n),
+                                             float(lr), float(wd), C.byref(loss) if want_loss else None),
+                   "arc_mlp_train_step")
+        return loss.value if want_loss else None
+
+
+def arc_mlp_eval(params, norm, X, Y, stream: Optional[int] = None) -> None:
+    p = _f32_host(params, MLP_NPARAMS)
+    q = _f32_host(norm, MLP_NNORM)
+    n = X.shape[0]
+    _mlp_check(load().arc_mlp_eval(p.ctypes.data, q.ctypes.data, C.c_void_p(_dev(X)), n, C.c_void_p(_dev(Y)),
+                                   C.c_void_p(stream or 0)), "arc_mlp_eval")
+
+
+def arc_mlp_features(nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float, X, stream: Optional[int] = None) -> None:
+    n = nH.numel()
+    _mlp_check(load().arc_mlp_features(*[C.c_void_p(_dev(a)) for a in (nH, xHI, xHeI, xHeII, T, gamma, heat)],
+                                       float(dt), n, C.c_void_p(_dev(X)), C.c_void_p(stream or 0)),
+               "arc_mlp_features")
+
+
+def arc_mlp_targets(x0, x1, T0, T1, Y, stream: Optional[int] = None) -> None:
+    n = T0.numel()
+    _mlp_check(load().arc_mlp_targets(*[C.c_void_p(_dev(a)) for a in (x0, x1, T0, T1)], n, C.c_void_p(_dev(Y)),
+                                      C.c_void_p(stream or 0)), "arc_mlp_targets")
+
+
+SURROGATE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "surrogate_cosmic.npz")
+
+
+def load_surrogate(path: Optional[str] = None):
+    """Trained surrogate weights: (params [ARC_MLP_NPARAMS], norm [ARC_MLP_NNORM], meta dict)."""
+    d = np.load(path or SURROGATE_FILE)
+    params = np.ascontiguousarray(d["params"], np.float32)
+    norm = np.ascontiguousarray(d["norm"], np.float32)
+    if params.size != MLP_NPARAMS or norm.size != MLP_NNORM:
+        raise ValueError("surrogate file does not match the network's shape")
+    return params, norm, json.loads(str(d["meta"]))
+
+
 def arc_last_error(ctx) -> str:
     return load().arc_last_error(C.c_void_p(ctx)).decode()
 
@@ -371,3 +493,6 @@ class Arc:
 
     def autotune(self, max_sources: int = 0, reps: int = 1) -> float:
         return arc_autotune(self.ctx, max_sources, reps)
+
+    def set_surrogate(self, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2):
+        arc_set_surrogate(self.ctx, params, norm, tol_x, tol_e)

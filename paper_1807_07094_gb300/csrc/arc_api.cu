@@ -34,7 +34,9 @@ struct Scalars {
     unsigned long long counters[CNT_ALL];
     unsigned long long nrec;
     double budget_out[2];
-    unsigned long long chem_counters[3];
+    unsigned long long chem_counters[4];   // substeps, fp64 substeps, capped, surrogate cells
+    unsigned int fb_count;                 // cells sent back to the plain solver
+    unsigned int pad1;
 };
 
 struct HostSource {
@@ -85,6 +87,11 @@ struct arc_ctx {
     bool graph_valid = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string err = "no error";
+    // chemistry surrogate
+    MlpDev* mlp = nullptr;
+    bool use_surrogate = false;
+    float tol_x = 5e-4f, tol_e = 1e-2f;
+    unsigned* fb_list = nullptr;
 };
 
 namespace {
@@ -365,8 +372,23 @@ arc_status enqueue_chem(arc_ctx* c, double dt) {
                              tg * tg * tg * tg);
     C.status = &c->scal->status;
     C.counters = c->scal->chem_counters;
+    C.list = nullptr;
+    C.list_count = nullptr;
     CK(cudaMemsetAsync(c->scal->chem_counters, 0, sizeof(c->scal->chem_counters), c->stream));
+    CK(cudaMemsetAsync(&c->scal->fb_count, 0, sizeof(unsigned), c->stream));
     CK(record_event(c, c->ev[2]));
+    if (c->use_surrogate) {
+        // network step for every cell; rejected cells -> plain sub-cycled solver
+        SurrogateArgs S;
+        S.w = c->mlp;
+        S.tol_x = c->tol_x;
+        S.tol_e = c->tol_e;
+        S.fb_list = c->fb_list;
+        S.fb_count = &c->scal->fb_count;
+        CK(launch_chem_surrogate(C, S, c->stream));
+        C.list = c->fb_list;
+        C.list_count = &c->scal->fb_count;
+    }
     CK(launch_chem(C, c->stream));
     CK(record_event(c, c->ev[3]));
     return ARC_OK;
@@ -614,6 +636,8 @@ arc_status arc_stats(arc_ctx* c, arc_stats_t* out) {
     out->chem_capped = S.chem_counters[2];
     out->segments_total = S.counters[CNT_SEG_TOTAL];
     out->traces_total = S.counters[CNT_TRACES_TOTAL];
+    out->surrogate_cells = S.chem_counters[3];
+    out->fallback_cells = c->use_surrogate ? S.fb_count : 0;
     float ms = 0.f;
     if (c->traced && cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out->trace_ms = ms;
     if (cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) out->chem_ms = ms;
@@ -645,6 +669,36 @@ arc_status arc_set_tuning(arc_ctx* c, int block_threads, int blocks_per_sm, int 
             return fail(c, ARC_E_INVALID, "stack_entries must be a power of two in 64..256");
         c->stack_log2 = lg;
     }
+    c->graph_valid = false;
+    return ARC_OK;
+}
+
+arc_status arc_set_surrogate(arc_ctx* c, const float* params, const float* norm, double tol_x, double tol_e) {
+    if (!c) return ARC_E_INVALID;
+    if (!params) {
+        c->use_surrogate = false;
+        c->graph_valid = false;
+        return ARC_OK;
+    }
+    if (!norm || !(tol_x > 0) || !(tol_e > 0)) return fail(c, ARC_E_INVALID, "surrogate: bad norm or tolerances");
+    for (int i = 0; i < ARC_MLP_NNORM; ++i)
+        if (!isfinite(norm[i]) || (((i >= MLP_IN && i < 2 * MLP_IN) || i >= 2 * MLP_IN + MLP_OUT) && !(norm[i] > 0)))
+            return fail(c, ARC_E_INVALID, "surrogate: normalisation entry %d invalid", i);
+    const size_t n3 = (size_t)c->n * c->n * c->n;
+    if (!c->mlp) CK(dalloc(&c->mlp, 1));
+    if (!c->fb_list) CK(dalloc(&c->fb_list, n3));
+    float* dp = nullptr;
+    CK(dalloc(&dp, (size_t)MLP_NPARAMS + ARC_MLP_NNORM));
+    cudaError_t e = cudaMemcpyAsync(dp, params, MLP_NPARAMS * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dp + MLP_NPARAMS, norm, ARC_MLP_NNORM * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_pack_mlp(dp, dp + MLP_NPARAMS, c->mlp, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(dp);
+    if (e != cudaSuccess) return fail(c, ARC_E_CUDA, "surrogate upload: %s", cudaGetErrorString(e));
+    c->tol_x = (float)tol_x;
+    c->tol_e = (float)tol_e;
+    c->use_surrogate = true;
     c->graph_valid = false;
     return ARC_OK;
 }
@@ -720,7 +774,7 @@ void arc_destroy(arc_ctx* c) {
     for (int i = 0; i < 4; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     void* ptrs[] = {c->nH, c->xHI, c->xHeI, c->xHeII, c->T, c->kappa, c->acc, c->gamma, c->heat,
-                    c->dsrc, c->seeds, c->qdata, c->qseq, c->scal, c->absorbed_part};
+                    c->dsrc, c->seeds, c->qdata, c->qseq, c->scal, c->absorbed_part, c->mlp, c->fb_list};
     for (void* q : ptrs) dfree(q);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -156,8 +156,76 @@ struct ChemArgs {
     float y, eps, xfloor, alpha_fixed, tcmb, compton_coef;
     int isothermal, coll_ion, compton;
     unsigned int* status;
-    unsigned long long* counters;  // substeps, fp64 substeps, capped
+    unsigned long long* counters;  // substeps, fp64 substeps, capped, surrogate-accepted cells (4)
+    // optional list of cells to update (the surrogate's fallback list)
+    const unsigned* list;
+    const unsigned* list_count;
 };
+
+// ---------------------------------------------------------------------------
+// Chemistry surrogate: per-cell MLP 12 -> 64 -> 64 -> 64 -> 4, SiLU, BF16
+// weights, FP32 accumulation.  Features (before normalisation):
+//   log10 nH, logit10 x_HI, logit10 x_HeI, logit10 x_HeII, log10 T,
+//   log10(Gamma_s + 1e-30) x3, log10(H_s + 1e-40) x3, log10 dt,
+// with logit10 x = log10(max(x, 1e-8) / max(1 - x, 1e-8)), which resolves
+// fractions near 0 and near 1 alike.
+// Targets (before normalisation): x_HI' - x_HI, x_HeI' - x_HeI,
+//   x_HeII' - x_HeII, log10(T'/T).
+// Flat FP32 parameter order: W1[64][12], b1[64], W2[64][64], b2[64],
+// W3[64][64], b3[64], W4[4][64], b4[4]  (MLP_NPARAMS floats).
+// The normalised FP32 features enter the first layer as two BF16 k-tiles,
+// v = hi + lo with hi = bf16(v), lo = bf16(v - hi), both multiplied by the
+// same BF16 W1: the inputs keep ~16 bits of precision at the cost of one
+// more 16-wide MMA k-step.
+// ---------------------------------------------------------------------------
+constexpr int MLP_IN = 12, MLP_H = 64, MLP_OUT = 4;
+constexpr int MLP_NPARAMS = MLP_H * MLP_IN + MLP_H + 2 * (MLP_H * MLP_H + MLP_H) + MLP_OUT * MLP_H + MLP_OUT;
+static_assert(MLP_NPARAMS == ARC_MLP_NPARAMS, "surrogate parameter count");
+static_assert(ARC_MLP_NNORM == 2 * MLP_IN + 3 * MLP_OUT, "surrogate normalisation block");
+// padded bf16 row strides (rows land on distinct shared-memory banks)
+constexpr int MLP_LD1 = 40, MLP_LDH = 72;
+struct MlpDev {
+    unsigned short W1[MLP_H * MLP_LD1];       // bf16 bits: [W1 | 0 0 0 0 | W1 | 0 0 0 0 | pad 8]
+    unsigned short W2[MLP_H * MLP_LDH];
+    unsigned short W3[MLP_H * MLP_LDH];
+    unsigned short W4[8 * MLP_LDH];           // rows 4..7 zero
+    float b1[MLP_H], b2[MLP_H], b3[MLP_H], b4[8];
+    float in_mu[MLP_IN], in_sd[MLP_IN], out_mu[MLP_OUT], out_sd[MLP_OUT], out_s[MLP_OUT];
+};
+static_assert(sizeof(MlpDev) % 16 == 0, "MlpDev is copied to shared memory in 16-byte words");
+
+__device__ __forceinline__ float logit10(float x) {
+    return log10f(fmaxf(x, 1e-8f) / fmaxf(1.0f - x, 1e-8f));
+}
+// Surrogate features of one cell, in the order of the public header.
+__device__ __forceinline__ void mlp_features(float nH, float xHI, float xHeI, float xHeII, float T,
+                                             const float (&G)[3], const float (&H)[3], float ldt,
+                                             float (&f)[MLP_IN]) {
+    f[0] = log10f(fmaxf(nH, 1e-30f));
+    f[1] = logit10(xHI);
+    f[2] = logit10(xHeI);
+    f[3] = logit10(xHeII);
+    f[4] = log10f(T);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        f[5 + q] = log10f(G[q] + 1e-30f);
+        f[8 + q] = log10f(H[q] + 1e-40f);
+    }
+    f[11] = ldt;
+}
+// Step change r_k from the network's k-th normalised output o.
+__device__ __forceinline__ float mlp_change(const MlpDev& w, int k, float o) {
+    return w.out_s[k] * sinhf(o * w.out_sd[k] + w.out_mu[k]);
+}
+struct SurrogateArgs {
+    const MlpDev* w;
+    float tol_x, tol_e;        // residual-check tolerances (abundance, relative energy)
+    unsigned* fb_list;         // cells that failed the check (for the plain solver)
+    unsigned* fb_count;
+};
+cudaError_t launch_chem_surrogate(const ChemArgs& c, const SurrogateArgs& s, cudaStream_t st);
+cudaError_t launch_pack_mlp(const float* params, const float* norm, MlpDev* out, cudaStream_t s);
+cudaError_t launch_mlp_eval(const MlpDev* w, const float* X, long long n, float* Y, cudaStream_t s);
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s);

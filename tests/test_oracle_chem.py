@@ -195,3 +195,34 @@ def test_collisional_ionisation_equilibrium():
         assert abs(x[0] - x_eq) < 1e-12
         x, *_, capped = run_cell(p, nH, 0.5, 0.0, 0.0, T, [0, 0, 0], [0, 0, 0], 1e4 / (a * nH))
         assert abs(x[0] - x_eq) < 2e-4, (T, x[0], x_eq)
+
+
+def test_refined_update_converges_to_riccati_solution():
+    """Pure H, isothermal, fixed alpha, constant Gamma: u = x_HII obeys
+    du/dt = Gamma (1 - u) - alpha n_H u^2, a Riccati equation with the closed
+    form u(t) = (u1 - u2 K e^{-s t}) / (1 - K e^{-s t}), s = alpha n_H (u1 - u2),
+    K = (u0 - u1) / (u0 - u2), u1 > 0 > u2 the roots of alpha n_H u^2 + Gamma u
+    - Gamma.  The uniformly refined update (every sub-step capped at dt/m)
+    converges to it at first order in 1/m; the paper's limiter alone bounds
+    the per-step change to 10 per cent and stays within 2e-2 of it."""
+    nH, alpha, G = 1e-2, 2.59e-13, 3e-14
+    p = params(alpha_B_fixed=alpha)
+    a, b = alpha * nH, G
+    u1 = (-b + math.sqrt(b * b + 4 * a * b)) / (2 * a)
+    u2 = (-b - math.sqrt(b * b + 4 * a * b)) / (2 * a)
+    u0 = 0.02
+    for tt in (0.5, 2.0):
+        t = tt / (a * (u1 - u2))
+        K = (u0 - u1) / (u0 - u2)
+        e = K * math.exp(-a * (u1 - u2) * t)
+        exact = 1 - (u1 - u2 * e) / (1 - e)     # x_HI
+        errs = {}
+        for m in (200, 400, 3200):
+            x, *_ = oracle.chem(p, np.array([nH]), np.array([1 - u0]), np.zeros(1), np.zeros(1),
+                                np.array([1e4]), np.array([[G], [0.0], [0.0]]), np.zeros((3, 1)), t, min_sub=m)
+            errs[m] = x[0] - exact
+        assert abs(errs[3200]) < 2e-4, errs
+        assert abs(errs[400]) < abs(errs[200]) < 2e-3, errs
+        assert abs(2 * errs[400] - errs[200]) < 0.03 * abs(errs[200]), errs   # first order in 1/m
+        x, *_ = run_cell(p, nH, 1 - u0, 0.0, 0.0, 1e4, [G, 0, 0], [0, 0, 0], t)
+        assert abs(errs[400]) < abs(x[0] - exact) < 0.02
