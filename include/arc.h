@@ -265,14 +265,19 @@ arc_status arc_autotune(arc_ctx* ctx, int max_sources, int reps, double* best_ms
 
 /* ------------------------------------------------------------------------
  * Chemistry surrogate (a learned stand-in for the sub-cycled update of
- * arc_chem_update; the paper has none).  Per cell an MLP
- * 12 -> 64 -> 64 -> 64 -> 4 with SiLU maps
- *   features  log10 nH, x_HI, x_HeI, x_HeII, log10 T, log10(Gamma_s + 1e-30) x3,
- *             log10(H_s + 1e-40) x3, log10 dt
- * to the step's changes r = (x_HI' - x_HI, x_HeI' - x_HeI, x_HeII' - x_HeII,
- * log10(T'/T)).  Inputs are normalised as (v - mu) / sd; the network's k-th
- * output o_k stands for r_k = s_k sinh(o_k sd_k + mu_k), so that small and
- * large changes are resolved alike.
+ * arc_chem_update; the paper has none).  Per cell a physics predictor -- the
+ * rate equations of Eq. (anninos) integrated exactly with the coefficients
+ * frozen at the start state (HI: one exponential; He: the HeI/HeII chain as
+ * a 2x2 linear system), and the energy from the trapezoidal heating of the
+ * start and predicted abundances minus the start cooling -- is corrected by
+ * an MLP 12 -> 64 -> 64 -> 64 -> 4 with SiLU that maps
+ *   features  log10 nH, logit10 x_HI, logit10 x_HeI, logit10 x_HeII, log10 T,
+ *             log10(Gamma_s + 1e-30) x3, log10(H_s + 1e-37) x3, log10 dt
+ *   (logit10 x = log10(max(x, 1e-8) / max(1 - x, 1e-8)))
+ * to the corrections r = (x_HI' - p_HI, x_HeI' - p_HeI, x_HeII' - p_HeII,
+ * log10(T'/p_T)).  Inputs are normalised as (v - mu) / sd; the network's
+ * k-th output o_k stands for r_k = s_k sinh(o_k sd_k + mu_k), so that small
+ * and large corrections are resolved alike.
  * Parameters: ARC_MLP_NPARAMS FP32 values in the order
  *   W1[64][12], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[4][64], b4[4];
  * normalisation: 36 FP32 values  in_mu[12], in_sd[12], out_mu[4], out_sd[4],
@@ -284,16 +289,21 @@ arc_status arc_autotune(arc_ctx* ctx, int max_sources, int reps, double* best_ms
 
 /*
  * arc_set_surrogate -- load surrogate parameters (host arrays) into the
- * context and use them in arc_chem_update / arc_step: every cell takes the
- * network's step unless a residual check rejects it -- the frozen-coefficient
- * solutions of Eq. (anninos) from the start state and from the predicted end
- * state must agree within tol_x (neutral fraction) and bracket the prediction,
- * and the start and end heating-minus-cooling rates must agree with the
- * predicted energy change within tol_e (relative) -- in which case the plain
- * sub-cycled solver updates that cell.  params = NULL switches the surrogate
- * off.  Synchronises.
+ * context and use them in arc_chem_update / arc_step.  Per cell the plain
+ * solver's cost is estimated from the predictor's changes (its limiter
+ * allows a fraction eps_sub of x_HI, x_HII and E per sub-step); cells
+ * estimated at <= gate sub-steps are left to the plain solver.  The others
+ * take the corrected prediction unless a residual check rejects it -- the
+ * step re-integrated in two halves with the coefficients frozen at 1/4 and
+ * 3/4 of the way from start to prediction must reproduce each predicted
+ * abundance within tol_x (helium per He atom) and the predicted energy
+ * within tol_e of the energy -- in which case the plain sub-cycled solver
+ * updates that cell.  params = NULL switches the surrogate off.
+ * tol_x, tol_e > 0, gate >= 0 (0: every cell tries the network).
+ * Synchronises.
  */
-arc_status arc_set_surrogate(arc_ctx* ctx, const float* params, const float* norm, double tol_x, double tol_e);
+arc_status arc_set_surrogate(arc_ctx* ctx, const float* params, const float* norm, double tol_x, double tol_e,
+                             double gate);
 
 /* Training.  A trainer holds FP32 master weights, AdamW moments and the
  * activations of one batch of up to max_batch samples (a multiple of 16). */
@@ -325,10 +335,13 @@ arc_status arc_mlp_eval(const float* params, const float* norm, const float* X, 
 arc_status arc_mlp_features(const float* nH, const float* xHI, const float* xHeI, const float* xHeII,
                             const float* T, const float* gamma, const float* heat, double dt, long long n, float* X,
                             void* stream);
-/* Surrogate targets from the states before (x0: 3 x n, T0) and after (x1, T1)
- * a chemistry step -> Y device n x 4. */
-arc_status arc_mlp_targets(const float* x0, const float* x1, const float* T0, const float* T1, long long n, float* Y,
-                           void* stream);
+/* Surrogate training targets on the context's chemistry switches: the
+ * corrections of a step's end state (x1: 3 x n fractions HI, HeI, HeII; T1)
+ * to the physics predictor started from (nH, x0: 3 x n, T0) with rates
+ * gamma, heat (3 x n each) over dt -> Y n x 4 (device arrays).  Runs on the
+ * context's stream and synchronises. */
+arc_status arc_mlp_targets(arc_ctx* ctx, const float* nH, const float* x0, const float* T0, const float* gamma,
+                           const float* heat, const float* x1, const float* T1, double dt, long long n, float* Y);
 
 /* Text of the most recent error on this context (never NULL). */
 const char* arc_last_error(const arc_ctx* ctx);

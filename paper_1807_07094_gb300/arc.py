@@ -91,7 +91,7 @@ _SIGS = {
                           [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "arc_destroy": ([C.c_void_p], None),
-    "arc_set_surrogate": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double], C.c_int),
+    "arc_set_surrogate": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double], C.c_int),
     "arc_mlp_trainer_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p], C.c_int),
     "arc_mlp_trainer_set_params": ([C.c_void_p, C.c_void_p], C.c_int),
     "arc_mlp_trainer_get_params": ([C.c_void_p, C.c_void_p], C.c_int),
@@ -101,7 +101,7 @@ _SIGS = {
     "arc_mlp_trainer_destroy": ([C.c_void_p], None),
     "arc_mlp_eval": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
     "arc_mlp_features": ([C.c_void_p] * 7 + [C.c_double, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
-    "arc_mlp_targets": ([C.c_void_p] * 4 + [C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
+    "arc_mlp_targets": ([C.c_void_p] * 8 + [C.c_double, C.c_longlong, C.c_void_p], C.c_int),
 }
 
 MLP_NPARAMS = 9412
@@ -326,13 +326,15 @@ def _dev(a):
     return p
 
 
-def arc_set_surrogate(ctx, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2) -> None:
+def arc_set_surrogate(ctx, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2,
+                      gate: float = 0.0) -> None:
     if params is None:
-        _check(ctx, load().arc_set_surrogate(C.c_void_p(ctx), None, None, 0.0, 0.0))
+        _check(ctx, load().arc_set_surrogate(C.c_void_p(ctx), None, None, 0.0, 0.0, 0.0))
         return
     p = _f32_host(params, MLP_NPARAMS)
     q = _f32_host(norm, MLP_NNORM)
-    _check(ctx, load().arc_set_surrogate(C.c_void_p(ctx), p.ctypes.data, q.ctypes.data, float(tol_x), float(tol_e)))
+    _check(ctx, load().arc_set_surrogate(C.c_void_p(ctx), p.ctypes.data, q.ctypes.data, float(tol_x), float(tol_e),
+                                         float(gate)))
 
 
 def _mlp_check(st, what):
@@ -400,10 +402,12 @@ def arc_mlp_features(nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float, X, stream:
                "arc_mlp_features")
 
 
-def arc_mlp_targets(x0, x1, T0, T1, Y, stream: Optional[int] = None) -> None:
+def arc_mlp_targets(ctx, nH, x0, T0, gamma, heat, x1, T1, dt: float, Y) -> None:
+    """Training targets (corrections to the physics predictor) of n cells;
+    runs on the context's stream and synchronises."""
     n = T0.numel()
-    _mlp_check(load().arc_mlp_targets(*[C.c_void_p(_dev(a)) for a in (x0, x1, T0, T1)], n, C.c_void_p(_dev(Y)),
-                                      C.c_void_p(stream or 0)), "arc_mlp_targets")
+    _check(ctx, load().arc_mlp_targets(C.c_void_p(ctx), *[C.c_void_p(_dev(a)) for a in (nH, x0, T0, gamma, heat, x1, T1)],
+                                       float(dt), n, C.c_void_p(_dev(Y))))
 
 
 SURROGATE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "surrogate_cosmic.npz")
@@ -494,5 +498,8 @@ class Arc:
     def autotune(self, max_sources: int = 0, reps: int = 1) -> float:
         return arc_autotune(self.ctx, max_sources, reps)
 
-    def set_surrogate(self, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2):
-        arc_set_surrogate(self.ctx, params, norm, tol_x, tol_e)
+    def set_surrogate(self, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2, gate: float = 0.0):
+        arc_set_surrogate(self.ctx, params, norm, tol_x, tol_e, gate)
+
+    def mlp_targets(self, nH, x0, T0, gamma, heat, x1, T1, dt: float, Y):
+        arc_mlp_targets(self.ctx, nH, x0, T0, gamma, heat, x1, T1, dt, Y)

@@ -90,7 +90,7 @@ struct arc_ctx {
     // chemistry surrogate
     MlpDev* mlp = nullptr;
     bool use_surrogate = false;
-    float tol_x = 5e-4f, tol_e = 1e-2f;
+    float tol_x = 5e-4f, tol_e = 1e-2f, gate = 0.0f;
     unsigned* fb_list = nullptr;
 };
 
@@ -346,17 +346,10 @@ arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
     return ARC_OK;
 }
 
-arc_status enqueue_chem(arc_ctx* c, double dt) {
+// chemistry switches and coefficients of the context (state arrays left to the caller)
+ChemArgs chem_args(const arc_ctx* c, double dt) {
     ChemArgs C;
     memset(&C, 0, sizeof C);
-    C.ncell = (long long)c->n * c->n * c->n;
-    C.nH = c->nH;
-    C.xHI = c->xHI;
-    C.xHeI = c->xHeI;
-    C.xHeII = c->xHeII;
-    C.T = c->T;
-    C.gamma = c->gamma;
-    C.heat = c->heat;
     C.dt = dt;
     C.y = (float)yfrac(c->p);
     C.eps = (float)c->p.eps_sub;
@@ -370,6 +363,19 @@ arc_status enqueue_chem(arc_ctx* c, double dt) {
     // 4 sigma_T a k / (m_e c) T_g^4 [erg/s/K per electron]
     C.compton_coef = (float)(4.0 * 6.6524587e-25 * 7.5657e-15 * K_BOLTZ / (9.1093837e-28 * 2.99792458e10) *
                              tg * tg * tg * tg);
+    return C;
+}
+
+arc_status enqueue_chem(arc_ctx* c, double dt) {
+    ChemArgs C = chem_args(c, dt);
+    C.ncell = (long long)c->n * c->n * c->n;
+    C.nH = c->nH;
+    C.xHI = c->xHI;
+    C.xHeI = c->xHeI;
+    C.xHeII = c->xHeII;
+    C.T = c->T;
+    C.gamma = c->gamma;
+    C.heat = c->heat;
     C.status = &c->scal->status;
     C.counters = c->scal->chem_counters;
     C.list = nullptr;
@@ -383,6 +389,7 @@ arc_status enqueue_chem(arc_ctx* c, double dt) {
         S.w = c->mlp;
         S.tol_x = c->tol_x;
         S.tol_e = c->tol_e;
+        S.gate = c->gate;
         S.fb_list = c->fb_list;
         S.fb_count = &c->scal->fb_count;
         CK(launch_chem_surrogate(C, S, c->stream));
@@ -673,14 +680,16 @@ arc_status arc_set_tuning(arc_ctx* c, int block_threads, int blocks_per_sm, int 
     return ARC_OK;
 }
 
-arc_status arc_set_surrogate(arc_ctx* c, const float* params, const float* norm, double tol_x, double tol_e) {
+arc_status arc_set_surrogate(arc_ctx* c, const float* params, const float* norm, double tol_x, double tol_e,
+                             double gate) {
     if (!c) return ARC_E_INVALID;
     if (!params) {
         c->use_surrogate = false;
         c->graph_valid = false;
         return ARC_OK;
     }
-    if (!norm || !(tol_x > 0) || !(tol_e > 0)) return fail(c, ARC_E_INVALID, "surrogate: bad norm or tolerances");
+    if (!norm || !(tol_x > 0) || !(tol_e > 0) || !(gate >= 0) || !isfinite(gate))
+        return fail(c, ARC_E_INVALID, "surrogate: bad norm, tolerances or gate");
     for (int i = 0; i < ARC_MLP_NNORM; ++i)
         if (!isfinite(norm[i]) || (((i >= MLP_IN && i < 2 * MLP_IN) || i >= 2 * MLP_IN + MLP_OUT) && !(norm[i] > 0)))
             return fail(c, ARC_E_INVALID, "surrogate: normalisation entry %d invalid", i);
@@ -698,8 +707,29 @@ arc_status arc_set_surrogate(arc_ctx* c, const float* params, const float* norm,
     if (e != cudaSuccess) return fail(c, ARC_E_CUDA, "surrogate upload: %s", cudaGetErrorString(e));
     c->tol_x = (float)tol_x;
     c->tol_e = (float)tol_e;
+    c->gate = (float)gate;
     c->use_surrogate = true;
     c->graph_valid = false;
+    return ARC_OK;
+}
+
+arc_status arc_mlp_targets(arc_ctx* c, const float* nH, const float* x0, const float* T0, const float* gamma,
+                           const float* heat, const float* x1, const float* T1, double dt, long long n, float* Y) {
+    if (!c) return ARC_E_INVALID;
+    if (!nH || !x0 || !T0 || !gamma || !heat || !x1 || !T1 || !Y || n < 1 || !(dt > 0) || !isfinite(dt))
+        return fail(c, ARC_E_INVALID, "arc_mlp_targets: null array, n < 1 or bad dt");
+    ChemArgs C = chem_args(c, dt);
+    C.ncell = n;
+    C.nH = const_cast<float*>(nH);
+    C.xHI = const_cast<float*>(x0);
+    C.xHeI = const_cast<float*>(x0 + n);
+    C.xHeII = const_cast<float*>(x0 + 2 * n);
+    C.T = const_cast<float*>(T0);
+    C.gamma = gamma;
+    C.heat = heat;
+    cudaError_t e = launch_mlp_targets(C, x1, T1, Y, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, ARC_E_CUDA, "arc_mlp_targets: %s", cudaGetErrorString(e));
     return ARC_OK;
 }
 

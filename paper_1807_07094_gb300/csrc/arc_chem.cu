@@ -35,30 +35,49 @@ struct Coef {
     float b0, b1, b2;     // collisional ionisation HI, HeI, HeII [cm^3/s]
 };
 
+// Transcendentals of the rate fits.  The plain solver evaluates them with
+// the accurate library functions; the surrogate's predictor and residual
+// check use the fast hardware forms, whose ~1e-6 relative error is far below
+// the check's tolerances.
+struct ExactMath {
+    static __device__ __forceinline__ float pow(float x, float e) { return powf(x, e); }
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float lg10(float x) { return log10f(x); }
+};
+struct FastMath {
+    static __device__ __forceinline__ float pow(float x, float e) { return __powf(x, e); }
+    static __device__ __forceinline__ float exp(float x) { return __expf(x); }
+    static __device__ __forceinline__ float lg10(float x) { return __log10f(x); }
+};
+
+template <class M>
 __device__ __forceinline__ float hg_alpha(float lam) {
-    return 2.753e-14f * powf(lam, 1.5f) / powf(1.0f + powf(lam * (1.0f / 2.740f), 0.407f), 2.242f);
+    return 2.753e-14f * M::pow(lam, 1.5f) / M::pow(1.0f + M::pow(lam * (1.0f / 2.740f), 0.407f), 2.242f);
 }
+template <class M>
 __device__ __forceinline__ float hg_recool(float T, float lam) {
-    return 3.435e-30f * T * powf(lam, 1.970f) / powf(1.0f + powf(lam * (1.0f / 2.250f), 0.376f), 3.720f);
+    return 3.435e-30f * T * M::pow(lam, 1.970f) / M::pow(1.0f + M::pow(lam * (1.0f / 2.250f), 0.376f), 3.720f);
 }
+template <class M>
 __device__ __forceinline__ float dielectronic_shape(float T) {
-    return powf(T, -1.5f) * expf(-4.7e5f / T) * (1.0f + 0.3f * expf(-9.4e4f / T));
+    return M::pow(T, -1.5f) * M::exp(-4.7e5f / T) * (1.0f + 0.3f * M::exp(-9.4e4f / T));
 }
 
+template <class M = ExactMath>
 __device__ __forceinline__ Coef coefficients(float T, const ChemArgs& C) {
     const float lHI = 2.0f * TH_HI / T, lHeI = 2.0f * TH_HEI / T, lHeII = 2.0f * TH_HEII / T;
     Coef r;
-    r.aH = C.alpha_fixed > 0.0f ? C.alpha_fixed : hg_alpha(lHI);
-    r.a2 = 1.26e-14f * powf(lHeI, 0.750f) + 1.90e-3f * dielectronic_shape(T);
-    r.a3 = 2.0f * hg_alpha(lHeII);
+    r.aH = C.alpha_fixed > 0.0f ? C.alpha_fixed : hg_alpha<M>(lHI);
+    r.a2 = 1.26e-14f * M::pow(lHeI, 0.750f) + 1.90e-3f * dielectronic_shape<M>(T);
+    r.a3 = 2.0f * hg_alpha<M>(lHeII);
     if (C.coll_ion) {
-        const float t32 = powf(T, -1.5f);
-        r.b0 = 21.11f * t32 * expf(-0.5f * lHI) * powf(lHI, -1.089f) /
-               powf(1.0f + powf(lHI * (1.0f / 0.354f), 0.874f), 1.101f);
-        r.b1 = 32.38f * t32 * expf(-0.5f * lHeI) * powf(lHeI, -1.146f) /
-               powf(1.0f + powf(lHeI * (1.0f / 0.416f), 0.987f), 1.056f);
-        r.b2 = 19.95f * t32 * expf(-0.5f * lHeII) * powf(lHeII, -1.089f) /
-               powf(1.0f + powf(lHeII * (1.0f / 0.553f), 0.735f), 1.275f);
+        const float t32 = M::pow(T, -1.5f);
+        r.b0 = 21.11f * t32 * M::exp(-0.5f * lHI) * M::pow(lHI, -1.089f) /
+               M::pow(1.0f + M::pow(lHI * (1.0f / 0.354f), 0.874f), 1.101f);
+        r.b1 = 32.38f * t32 * M::exp(-0.5f * lHeI) * M::pow(lHeI, -1.146f) /
+               M::pow(1.0f + M::pow(lHeI * (1.0f / 0.416f), 0.987f), 1.056f);
+        r.b2 = 19.95f * t32 * M::exp(-0.5f * lHeII) * M::pow(lHeII, -1.089f) /
+               M::pow(1.0f + M::pow(lHeII * (1.0f / 0.553f), 0.735f), 1.275f);
     } else {
         r.b0 = r.b1 = r.b2 = 0.0f;
     }
@@ -67,6 +86,7 @@ __device__ __forceinline__ Coef coefficients(float T, const ChemArgs& C) {
 
 // Cooling per hydrogen atom [erg/s]: Lambda / n_H for abundances a0 = HI,
 // a1 = HeI, a2 = HeII per H and electrons xe per H.
+template <class M = ExactMath>
 __device__ __forceinline__ float cooling_per_h(float T, float nH, float a0, float a1, float a2,
                                                float xe, const Coef& r, const ChemArgs& C) {
     const float lHI = 2.0f * TH_HI / T, lHeI = 2.0f * TH_HEI / T, lHeII = 2.0f * TH_HEII / T;
@@ -74,12 +94,12 @@ __device__ __forceinline__ float cooling_per_h(float T, float nH, float a0, floa
     const float a3 = fmaxf(C.y - a1 - a2, 0.0f);          // HeIII per H
     const float nxe = nH * xe;                             // n_e [cm^-3]
     float L = r.b0 * a0 * (KB * TH_HI) + r.b1 * a1 * (KB * TH_HEI) + r.b2 * a2 * (KB * TH_HEII);
-    L += hg_recool(T, lHI) * aHII + 1.26e-14f * powf(lHeI, 0.750f) * KB * T * a2 +
-         8.0f * hg_recool(T, lHeII) * a3 + 1.24e-13f * dielectronic_shape(T) * a2;
+    L += hg_recool<M>(T, lHI) * aHII + 1.26e-14f * M::pow(lHeI, 0.750f) * KB * T * a2 +
+         8.0f * hg_recool<M>(T, lHeII) * a3 + 1.24e-13f * dielectronic_shape<M>(T) * a2;
     const float sq = 1.0f + sqrtf(T * 1e-5f);
-    L += 7.5e-19f * expf(-118348.0f / T) / sq * a0 + 5.54e-17f * powf(T, -0.397f) * expf(-473638.0f / T) / sq * a2;
-    const float lg = log10f(T) - 5.5f;
-    const float gff = 1.1f + 0.34f * expf(-lg * lg * (1.0f / 3.0f));
+    L += 7.5e-19f * M::exp(-118348.0f / T) / sq * a0 + 5.54e-17f * M::pow(T, -0.397f) * M::exp(-473638.0f / T) / sq * a2;
+    const float lg = M::lg10(T) - 5.5f;
+    const float gff = 1.1f + 0.34f * M::exp(-lg * lg * (1.0f / 3.0f));
     L += 1.42e-27f * gff * sqrtf(T) * (aHII + a2 + 4.0f * a3);
     L *= nxe;
     if (C.compton) L += C.compton_coef * (T - C.tcmb) * xe;
@@ -213,7 +233,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
 }
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+// SiLU for the inference tiles: the fast exponential and a correctly rounded
+// reciprocal keep its relative error near 1e-7, far below the BF16 rounding
+// (2^-9) that every activation takes next
+__device__ __forceinline__ float silu(float z) { return z * __frcp_rn(1.0f + __expf(-z)); }
 
 // out = SiLU(in W^T + b) for a 16-row tile; in has KT 16-wide k-tiles, out 64 columns
 template <int KT>
@@ -240,66 +263,146 @@ __device__ __forceinline__ void dense_silu(const uint32_t (&ain)[KT][4], uint32_
     }
 }
 
-// Residual check of a surrogate step (start abundances a0..a2 per H and T;
-// prediction s0..s2, sT).  The rate equations of Eq. (anninos) are linear in
-// the abundances once n_e and T are fixed; with the coefficients frozen at
-// the midpoint of the step (abundances and T averaged between start and
-// prediction) they are integrated exactly over dt:
+// The rate equations of Eq. (anninos) are linear in the abundances once n_e
+// and T are fixed.  With the coefficients frozen (evaluated at abundances
+// c0..c2 per H and temperature Tc) they integrate exactly over dt:
 //   HI:  a0' = D - C a0,
-//   He:  v' = A v + c for v = (HeI, HeII), HeIII = y - HeI - HeII, whose
-//        matrix has real eigenvalues lam1 >= lam2 (the three-state chain is
-//        a birth-death process, similar to a symmetric matrix),
+//   He:  v' = A v + c for v = (HeI, HeII) per H, HeIII = y - HeI - HeII,
+//        whose matrix has real eigenvalues lam1 >= lam2 (the three-state
+//        chain is a birth-death process, similar to a symmetric matrix),
 // both written v(dt) = v0 + phi(A) (A v0 + c), phi(A) = int_0^dt e^{A t} dt,
-// which stays finite as the rates vanish.  The prediction is accepted when
-// every abundance agrees with this solution within tol_x (He per He atom)
-// and its energy with E0 + dt Edot(midpoint) within tol_e of the energy.
+// which stays finite as the rates vanish.
 
-// g(u) = (e^u - 1) / u and its derivative, for u <= 0
-__device__ __forceinline__ float g_phi(float u) { return fabsf(u) < 1e-4f ? 1.0f + 0.5f * u : expm1f(u) / u; }
-__device__ __forceinline__ float g_phi_d(float u) {
+// phi1(u) = (e^u - 1) / u and phi2(u) = (e^u - 1 - u) / u^2 (the integral of
+// phi1(u s) s over s in [0, 1]) with their derivatives, for u <= 0: series
+// for |u| < 0.1, where the closed forms cancel; beyond, the closed forms with
+// the fast exponential keep a relative error below ~1e-4 (surrogate use only)
+__device__ __forceinline__ float phi1(float u) {
+    if (fabsf(u) < 0.1f) return 1.0f + u * (0.5f + u * (1.0f / 6.0f + u * (1.0f / 24.0f + u * (1.0f / 120.0f))));
+    return __fdividef(__expf(u) - 1.0f, u);
+}
+__device__ __forceinline__ float phi1_d(float u) {
     if (fabsf(u) < 0.1f) return 0.5f + u * (1.0f / 3.0f + u * (0.125f + u * (1.0f / 30.0f + u * (1.0f / 144.0f))));
-    return (u * expf(u) - expm1f(u)) / (u * u);
+    const float e = __expf(u);
+    return __fdividef(u * e - (e - 1.0f), u * u);
+}
+__device__ __forceinline__ float phi2(float u) {
+    if (fabsf(u) < 0.1f) return 0.5f + u * (1.0f / 6.0f + u * (1.0f / 24.0f + u * (1.0f / 120.0f)));
+    return __fdividef(__expf(u) - 1.0f - u, u * u);
+}
+__device__ __forceinline__ float phi2_d(float u) {
+    if (fabsf(u) < 0.1f) return 1.0f / 6.0f + u * (1.0f / 12.0f + u * (1.0f / 40.0f + u * (1.0f / 180.0f)));
+    return __fdividef(phi1(u) - 2.0f * phi2(u), u);
+}
+// divided difference f[u1, u2] for u1 >= u2, by the derivative at the midpoint
+// where the two are close
+template <float (*F)(float), float (*FD)(float)>
+__device__ __forceinline__ float divdiff(float u1, float u2) {
+    const float du = u1 - u2, um = 0.5f * (u1 + u2);
+    return du > 1e-2f * fmaxf(1.0f, fabsf(um)) ? (F(u1) - F(u2)) / du : FD(um);
 }
 
+// Frozen-coefficient solution over dt from (a0, a1, a2) with coefficients
+// evaluated at abundances (c0, c1, c2) and rates r; with ints != nullptr
+// also the time integrals int_0^dt a_s dt (for the photoheating).
+// Matrix functions of the 2x2 He system use f(A dt) = f(u2) I +
+// f[u1, u2] dt (A - lam2 I), u = lam dt.
+__device__ void frozen_abundances(float nH, float y, float c0, float c1, float c2, const Coef& r,
+                                  const float (&G)[3], float a0, float a1, float a2, float dt, float& e0,
+                                  float& e1, float& e2, float* ints = nullptr) {
+    const float ne = nH * ((1.0f - c0) + c2 + 2.0f * (y - c1 - c2));
+    const float CH = G[0] + (r.b0 + r.aH) * ne, DH = r.aH * ne;
+    const float fH = DH - CH * a0;
+    e0 = a0 + dt * phi1(-CH * dt) * fH;
+    e1 = a1;
+    e2 = a2;
+    if (ints) {
+        ints[0] = dt * a0 + dt * dt * phi2(-CH * dt) * fH;
+        ints[1] = dt * a1;
+        ints[2] = dt * a2;
+    }
+    if (!(y > 0.0f)) return;
+    // helium chain: A = [[-k1, r2], [k1 - r3, -(k2 + r2 + r3)]], c = (0, r3 y)
+    const float k1 = G[1] + r.b1 * ne, k2 = G[2] + r.b2 * ne, r2 = r.a2 * ne, r3 = r.a3 * ne;
+    const float A11 = -k1, A12 = r2, A21 = k1 - r3, A22 = -(k2 + r2 + r3);
+    const float tr = A11 + A22;
+    const float det = k1 * (k2 + r3) + r2 * r3;   // = A11 A22 - A12 A21, all terms >= 0
+    const float hd = 0.5f * (A11 - A22);
+    const float mu = sqrtf(fmaxf(hd * hd + A12 * A21, 0.0f));
+    const float l2 = 0.5f * tr - mu;               // most negative eigenvalue
+    const float l1 = l2 < 0.0f ? fminf(det / l2, 0.0f) : 0.0f;
+    const float u1 = l1 * dt, u2 = l2 * dt;
+    const float f1 = A11 * a1 + A12 * a2, f2 = A21 * a1 + A22 * a2 + r3 * y;   // v' at the start
+    const float m1 = (A11 - l2) * f1 + A12 * f2, m2 = A21 * f1 + (A22 - l2) * f2;   // (A - lam2 I) f
+    // v(dt) = v0 + dt phi1(A dt) f
+    const float q0 = dt * phi1(u2), q1 = dt * dt * divdiff<phi1, phi1_d>(u1, u2);
+    e1 = fminf(fmaxf(a1 + q0 * f1 + q1 * m1, 0.0f), y);
+    e2 = fminf(fmaxf(a2 + q0 * f2 + q1 * m2, 0.0f), y - e1);
+    if (ints) {
+        // int v dt = dt v0 + dt^2 phi2(A dt) f
+        const float w0 = dt * dt * phi2(u2), w1 = dt * dt * dt * divdiff<phi2, phi2_d>(u1, u2);
+        ints[1] = dt * a1 + w0 * f1 + w1 * m1;
+        ints[2] = dt * a2 + w0 * f2 + w1 * m2;
+    }
+}
+
+// Physics predictor of a step, which the network corrects: abundances from
+// the rate equations frozen at the start state; energy from the photoheating
+// of those abundance histories minus the cooling of the start state.
+__device__ void surrogate_predictor(float nH, float y, float a0, float a1, float a2, float T, const float (&G)[3],
+                                    const float (&H)[3], float dt, const ChemArgs& C, float& p0, float& p1,
+                                    float& p2, float& pT) {
+    const Coef r = coefficients<FastMath>(T, C);
+    float I[3];
+    frozen_abundances(nH, y, a0, a1, a2, r, G, a0, a1, a2, dt, p0, p1, p2, I);
+    pT = T;
+    if (!C.isothermal) {
+        const float xe0 = (1.0f - a0) + a2 + 2.0f * (y - a1 - a2);
+        const float xe1 = (1.0f - p0) + p2 + 2.0f * (y - p1 - p2);
+        const float E0 = 1.5f * KB * T * (1.0f + y + xe0);
+        const float E1 = E0 + (I[0] * H[0] + I[1] * H[1] + I[2] * H[2]) -
+                         dt * cooling_per_h<FastMath>(T, nH, a0, a1, a2, xe0, r, C);
+        pT = fmaxf(E1 / (1.5f * KB * (1.0f + y + xe1)), T_FLOOR);
+    }
+}
+
+// Residual check of a surrogate step (start a0..a2 per H and T; prediction
+// s0..s2, sT).  The step is re-integrated in two halves, each with the
+// frozen-coefficient solution whose coefficients are taken on the straight
+// path from start to prediction at 1/4 and 3/4 of the step (a second-order
+// integrator whose coefficients come from the prediction itself).  Every
+// predicted abundance must agree with it within tol_x (He per He atom), and
+// the predicted energy with E0 plus the photoheating of its abundance
+// histories minus the cooling at the two points, within tol_e of the energy.
+// One half-step evaluation (the midpoint alone) is fooled where the
+// coefficients vary strongly along the step, e.g. an ionisation front
+// crossing the cell; two are not, on the cosmic-field states tested.
 __device__ bool surrogate_accept(float nH, float y, float a0, float a1, float a2, float T, float s0, float s1,
                                  float s2, float sT, const float (&G)[3], const float (&H)[3], float dt,
                                  const ChemArgs& C, float tol_x, float tol_e) {
-    const float m0 = 0.5f * (a0 + s0), m1 = 0.5f * (a1 + s1), m2 = 0.5f * (a2 + s2);
-    const float Tm = 0.5f * (T + sT);
-    const float xe = (1.0f - m0) + m2 + 2.0f * (y - m1 - m2);
-    const Coef r = coefficients(Tm, C);
-    const float ne = nH * xe;
-    // hydrogen
-    const float CH = G[0] + (r.b0 + r.aH) * ne, DH = r.aH * ne;
-    const float e0 = a0 + dt * g_phi(-CH * dt) * (DH - CH * a0);
-    if (!(fabsf(e0 - s0) <= tol_x)) return false;
-    if (y > 0.0f) {
-        // helium chain: A = [[-k1, r2], [k1 - r3, -(k2 + r2 + r3)]], c = (0, r3 y)
-        const float k1 = G[1] + r.b1 * ne, k2 = G[2] + r.b2 * ne, r2 = r.a2 * ne, r3 = r.a3 * ne;
-        const float A11 = -k1, A12 = r2, A21 = k1 - r3, A22 = -(k2 + r2 + r3);
-        const float tr = A11 + A22;
-        const float det = k1 * (k2 + r3) + r2 * r3;   // = A11 A22 - A12 A21, all terms >= 0
-        const float hd = 0.5f * (A11 - A22);
-        const float mu = sqrtf(fmaxf(hd * hd + A12 * A21, 0.0f));
-        const float l2 = 0.5f * tr - mu;               // most negative eigenvalue
-        const float l1 = l2 < 0.0f ? fminf(det / l2, 0.0f) : 0.0f;
-        const float u1 = l1 * dt, u2 = l2 * dt, du = u1 - u2;
-        // phi(A) = dt g(u2) I + P1 (A - l2 I), P1 = dt^2 (g(u1) - g(u2)) / (u1 - u2)
-        const float um = 0.5f * (u1 + u2);
-        const float P1 = dt * dt * (du > 1e-2f * fmaxf(1.0f, fabsf(um)) ? (g_phi(u1) - g_phi(u2)) / du : g_phi_d(um));
-        const float p0 = dt * g_phi(u2);
-        const float f1 = A11 * a1 + A12 * a2, f2 = A21 * a1 + A22 * a2 + r3 * y;   // v' at the start
-        const float e1 = a1 + p0 * f1 + P1 * ((A11 - l2) * f1 + A12 * f2);
-        const float e2 = a2 + p0 * f2 + P1 * (A21 * f1 + (A22 - l2) * f2);
-        const float th = tol_x * y;
-        if (!(fabsf(e1 - s1) <= th) || !(fabsf(e2 - s2) <= th)) return false;
+    float e0 = a0, e1 = a1, e2 = a2;
+    float dE = 0.0f;
+    const float h = 0.5f * dt;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float f = j ? 0.75f : 0.25f;
+        const float m0 = a0 + f * (s0 - a0), m1 = a1 + f * (s1 - a1), m2 = a2 + f * (s2 - a2);
+        const float Tm = T + f * (sT - T);
+        const Coef r = coefficients<FastMath>(Tm, C);
+        float I[3];
+        frozen_abundances(nH, y, m0, m1, m2, r, G, e0, e1, e2, h, e0, e1, e2, I);
+        if (!C.isothermal) {
+            const float xe = (1.0f - m0) + m2 + 2.0f * (y - m1 - m2);
+            dE += (I[0] * H[0] + I[1] * H[1] + I[2] * H[2]) - h * cooling_per_h<FastMath>(Tm, nH, m0, m1, m2, xe, r, C);
+        }
     }
+    const float th = tol_x * y;
+    if (!(fabsf(e0 - s0) <= tol_x) || !(fabsf(e1 - s1) <= th) || !(fabsf(e2 - s2) <= th)) return false;
     if (!C.isothermal) {
         const float xe0 = (1.0f - a0) + a2 + 2.0f * (y - a1 - a2);
         const float xe1 = (1.0f - s0) + s2 + 2.0f * (y - s1 - s2);
         const float E0 = 1.5f * KB * T * (1.0f + y + xe0), E1 = 1.5f * KB * sT * (1.0f + y + xe1);
-        const float edot = (m0 * H[0] + m1 * H[1] + m2 * H[2]) - cooling_per_h(Tm, nH, m0, m1, m2, xe, r, C);
-        if (!(fabsf(E1 - E0 - dt * edot) <= tol_e * fmaxf(E0, E1))) return false;
+        if (!(fabsf(E1 - E0 - dE) <= tol_e * fmaxf(E0, E1))) return false;
     }
     return true;
 }
@@ -383,10 +486,17 @@ __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_eval(const MlpDev* wp, c
     }
 }
 
+// Surrogate chemistry update: every warp takes 32 cells at a time (one per
+// lane for the scalar work, two 16-row tiles for the network).  Per cell:
+// the physics predictor; the plain solver's cost estimated from the
+// predicted changes (its limiter allows a fraction eps of x_HI, x_HII and E
+// per sub-step); cheap cells (estimate <= S.gate sub-steps) go to the plain
+// solver's list untouched; the others take the corrected prediction if the
+// residual check accepts it, else they join the list too.
 __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_chem(const ChemArgs C, const SurrogateArgs S) {
     __shared__ __align__(16) MlpDev w;
-    __shared__ __align__(16) unsigned short feat[MLP_WARPS][16 * MLP_LD1];
-    __shared__ float outv[MLP_WARPS][16][4];
+    __shared__ __align__(16) unsigned short feat[MLP_WARPS][32 * MLP_LD1];
+    __shared__ float outv[MLP_WARPS][32][4];
     {
         const uint4* src = reinterpret_cast<const uint4*>(S.w);
         uint4* dst = reinterpret_cast<uint4*>(&w);
@@ -399,19 +509,21 @@ __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_chem(const ChemArgs C, c
     const float dt = (float)C.dt;
     const float ldt = log10f(dt);
     unsigned accepted = 0;
-    const long long ntiles = (C.ncell + 15) / 16;
+    const long long ngroups = (C.ncell + 31) / 32;
     unsigned short* ft = feat[wid];
-    for (long long tile = (long long)blockIdx.x * MLP_WARPS + wid; tile < ntiles;
-         tile += (long long)gridDim.x * MLP_WARPS) {
-        const long long c = tile * 16 + (lane & 15);
-        bool valid = lane < 16 && c < C.ncell;
-        float nH = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, T = 1.f;
+    for (long long grp = (long long)blockIdx.x * MLP_WARPS + wid; grp < ngroups;
+         grp += (long long)gridDim.x * MLP_WARPS) {
+        const long long c = grp * 32 + lane;
+        bool valid = c < C.ncell;
+        float nH = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, T = 1.f, xHeI = 0.f, xHeII = 0.f;
         float G[3] = {0.f, 0.f, 0.f}, H[3] = {0.f, 0.f, 0.f};
         if (valid) {
             nH = C.nH[c];
             a0 = C.xHI[c];
-            a1 = y * C.xHeI[c];
-            a2 = y * C.xHeII[c];
+            xHeI = C.xHeI[c];
+            xHeII = C.xHeII[c];
+            a1 = y * xHeI;
+            a2 = y * xHeII;
             T = C.T[c];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -420,23 +532,47 @@ __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_chem(const ChemArgs C, c
             }
             valid = nH > 0.f;   // empty cells are left as they are, as by the plain update
         }
-        if (lane < 16) {
+        {
             float f[MLP_IN];
-            mlp_features(nH, a0, valid ? C.xHeI[c] : 0.f, valid ? C.xHeII[c] : 0.f, T, G, H, ldt, f);
+            mlp_features(nH, a0, xHeI, xHeII, T, G, H, ldt, f);
             store_features(ft + lane * MLP_LD1, f, w);
         }
         __syncwarp();
         mlp_tile(ft, w, outv[wid], g, t4);
+        mlp_tile(ft + 16 * MLP_LD1, w, outv[wid] + 16, g, t4);
         __syncwarp();
+        bool fallback = false;
         if (valid) {
-            float d[MLP_OUT];
+            float p0, p1, p2, pT;
+            surrogate_predictor(nH, y, a0, a1, a2, T, G, H, dt, C, p0, p1, p2, pT);
+            // sub-steps the plain solver would take, from the predicted changes
+            float nest = fabsf(p0 - a0) / (C.eps * fmaxf(fminf(fminf(a0, 1.0f - a0), fminf(p0, 1.0f - p0)), C.xfloor));
+            if (!C.isothermal) {
+                const float E0 = T * (1.0f + y + (1.0f - a0) + a2 + 2.0f * (y - a1 - a2));
+                const float E1 = pT * (1.0f + y + (1.0f - p0) + p2 + 2.0f * (y - p1 - p2));
+                nest = fmaxf(nest, fabsf(E1 - E0) / (C.eps * fminf(E0, E1)));
+            }
+            bool take = false;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, sT = T;
+            if (nest > S.gate) {
+                float d[MLP_OUT];
 #pragma unroll
-            for (int k = 0; k < MLP_OUT; ++k) d[k] = mlp_change(w, k, outv[wid][lane][k]);
-            const float s0 = fminf(fmaxf(a0 + d[0], 0.f), 1.f);
-            const float s1 = fminf(fmaxf(a1 + y * d[1], 0.f), y);
-            const float s2 = fminf(fmaxf(a2 + y * d[2], 0.f), y - s1);
-            const float sT = C.isothermal ? T : fmaxf(T * exp10f(d[3]), T_FLOOR);
-            if (surrogate_accept(nH, y, a0, a1, a2, T, s0, s1, s2, sT, G, H, dt, C, S.tol_x, S.tol_e)) {
+                for (int k = 0; k < MLP_OUT; ++k) d[k] = mlp_change(w, k, outv[wid][lane][k]);
+                s0 = fminf(fmaxf(p0 + d[0], 0.f), 1.f);
+                s1 = fminf(fmaxf(p1 + y * d[1], 0.f), y);
+                s2 = fminf(fmaxf(p2 + y * d[2], 0.f), y - s1);
+                sT = C.isothermal ? T : fmaxf(pT * exp10f(d[3]), T_FLOOR);
+                // a large learned correction marks a step the frozen-coefficient
+                // physics misses, and an ionisation front crossing the cell
+                // (x_HI or T changing by a large factor within the step) one
+                // where the two-half-step check itself is off by ~1e-3: both
+                // stay with the plain solver
+                const bool small = fabsf(d[0]) <= 4.0f * S.tol_x && fabsf(d[1]) <= 4.0f * S.tol_x &&
+                                   fabsf(d[2]) <= 4.0f * S.tol_x && fabsf(d[3]) <= 1.7f * S.tol_e &&
+                                   fabsf(s0 - a0) <= 0.1f && sT <= 10.0f * T && T <= 10.0f * sT;
+                take = small && surrogate_accept(nH, y, a0, a1, a2, T, s0, s1, s2, sT, G, H, dt, C, S.tol_x, S.tol_e);
+            }
+            if (take) {
                 C.xHI[c] = s0;
                 if (y > 0.f) {
                     C.xHeI[c] = s1 / y;
@@ -445,9 +581,16 @@ __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_chem(const ChemArgs C, c
                 C.T[c] = sT;
                 accepted++;
             } else {
-                const unsigned slot = atomicAdd(S.fb_count, 1u);
-                S.fb_list[slot] = (unsigned)c;
+                fallback = true;
             }
+        }
+        // the warp's rejected cells join the plain solver's list as one run
+        const unsigned fbm = __ballot_sync(0xFFFFFFFFu, fallback);
+        if (fbm) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(S.fb_count, (unsigned)__popc(fbm));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (fallback) S.fb_list[base + __popc(fbm & ((1u << lane) - 1u))] = (unsigned)c;
         }
         __syncwarp();
     }
@@ -499,9 +642,9 @@ __global__ void k_pack_mlp(const float* P, const float* norm, MlpDev* out) {
 }  // namespace
 
 cudaError_t launch_chem_surrogate(const ChemArgs& c, const SurrogateArgs& s, cudaStream_t st) {
-    long long tiles = (c.ncell + 15) / 16;
-    long long blocks = (tiles + MLP_WARPS - 1) / MLP_WARPS;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    // grid-stride over groups of 32 cells; the weights are staged once per block
+    long long blocks = ((c.ncell + 31) / 32 + MLP_WARPS - 1) / MLP_WARPS;
+    if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     k_mlp_chem<<<(int)blocks, MLP_WARPS * 32, 0, st>>>(c, s);
     return cudaGetLastError();
@@ -517,6 +660,38 @@ cudaError_t launch_mlp_eval(const MlpDev* w, const float* X, long long n, float*
 
 cudaError_t launch_pack_mlp(const float* params, const float* norm, MlpDev* out, cudaStream_t s) {
     k_pack_mlp<<<1, 256, 0, s>>>(params, norm, out);
+    return cudaGetLastError();
+}
+
+// Surrogate training targets: the corrections of the converged step (x1, T1)
+// to the physics predictor, Y[n][4] = (x_HI' - p0, x_HeI' - p1 / y,
+// x_HeII' - p2 / y, log10(T' / pT)).  C holds the start state.
+__global__ void k_mlp_targets(const ChemArgs C, const float* x1, const float* T1, float* Y) {
+    const float y = C.y, dt = (float)C.dt;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float nH = C.nH[c];
+        const float a0 = C.xHI[c], a1 = y * C.xHeI[c], a2 = y * C.xHeII[c], T = C.T[c];
+        float G[3], H[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            G[q] = C.gamma[q * C.ncell + c];
+            H[q] = C.heat[q * C.ncell + c];
+        }
+        float p0, p1, p2, pT;
+        surrogate_predictor(nH, y, a0, a1, a2, T, G, H, dt, C, p0, p1, p2, pT);
+        Y[c * MLP_OUT + 0] = x1[c] - p0;
+        Y[c * MLP_OUT + 1] = y > 0.f ? x1[C.ncell + c] - p1 / y : 0.f;
+        Y[c * MLP_OUT + 2] = y > 0.f ? x1[2 * C.ncell + c] - p2 / y : 0.f;
+        Y[c * MLP_OUT + 3] = C.isothermal ? 0.f : log10f(T1[c] / pT);
+    }
+}
+
+cudaError_t launch_mlp_targets(const ChemArgs& c, const float* x1, const float* T1, float* Y, cudaStream_t s) {
+    long long blocks = (c.ncell + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_mlp_targets<<<(int)blocks, 256, 0, s>>>(c, x1, T1, Y);
     return cudaGetLastError();
 }
 

@@ -166,11 +166,14 @@ struct ChemArgs {
 // Chemistry surrogate: per-cell MLP 12 -> 64 -> 64 -> 64 -> 4, SiLU, BF16
 // weights, FP32 accumulation.  Features (before normalisation):
 //   log10 nH, logit10 x_HI, logit10 x_HeI, logit10 x_HeII, log10 T,
-//   log10(Gamma_s + 1e-30) x3, log10(H_s + 1e-40) x3, log10 dt,
+//   log10(Gamma_s + 1e-30) x3, log10(H_s + 1e-37) x3, log10 dt,
 // with logit10 x = log10(max(x, 1e-8) / max(1 - x, 1e-8)), which resolves
 // fractions near 0 and near 1 alike.
-// Targets (before normalisation): x_HI' - x_HI, x_HeI' - x_HeI,
-//   x_HeII' - x_HeII, log10(T'/T).
+// The network corrects a physics predictor (p0..p2, pT: the rate equations
+// integrated exactly with the coefficients frozen at the start state, and
+// the energy from trapezoidal heating minus the start cooling).  Targets
+// (before normalisation): x_HI' - p0, x_HeI' - p1/y, x_HeII' - p2/y,
+// log10(T'/pT).
 // Flat FP32 parameter order: W1[64][12], b1[64], W2[64][64], b2[64],
 // W3[64][64], b3[64], W4[4][64], b4[4]  (MLP_NPARAMS floats).
 // The normalised FP32 features enter the first layer as two BF16 k-tiles,
@@ -194,22 +197,26 @@ struct MlpDev {
 };
 static_assert(sizeof(MlpDev) % 16 == 0, "MlpDev is copied to shared memory in 16-byte words");
 
+// Surrogate features use the hardware base-2 logarithm (absolute error
+// ~1e-7 in log10, below the ~2^-16 relative resolution the split BF16
+// inputs keep).
+__device__ __forceinline__ float flog10(float x) { return __log2f(x) * 0.30102999566398120f; }
 __device__ __forceinline__ float logit10(float x) {
-    return log10f(fmaxf(x, 1e-8f) / fmaxf(1.0f - x, 1e-8f));
+    return flog10(__fdividef(fmaxf(x, 1e-8f), fmaxf(1.0f - x, 1e-8f)));
 }
 // Surrogate features of one cell, in the order of the public header.
 __device__ __forceinline__ void mlp_features(float nH, float xHI, float xHeI, float xHeII, float T,
                                              const float (&G)[3], const float (&H)[3], float ldt,
                                              float (&f)[MLP_IN]) {
-    f[0] = log10f(fmaxf(nH, 1e-30f));
+    f[0] = flog10(fmaxf(nH, 1e-30f));
     f[1] = logit10(xHI);
     f[2] = logit10(xHeI);
     f[3] = logit10(xHeII);
-    f[4] = log10f(T);
+    f[4] = flog10(T);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        f[5 + q] = log10f(G[q] + 1e-30f);
-        f[8 + q] = log10f(H[q] + 1e-40f);
+        f[5 + q] = flog10(G[q] + 1e-30f);
+        f[8 + q] = flog10(H[q] + 1e-37f);
     }
     f[11] = ldt;
 }
@@ -220,12 +227,14 @@ __device__ __forceinline__ float mlp_change(const MlpDev& w, int k, float o) {
 struct SurrogateArgs {
     const MlpDev* w;
     float tol_x, tol_e;        // residual-check tolerances (abundance, relative energy)
+    float gate;                // cells the plain solver handles in <= gate sub-steps skip the network
     unsigned* fb_list;         // cells that failed the check (for the plain solver)
     unsigned* fb_count;
 };
 cudaError_t launch_chem_surrogate(const ChemArgs& c, const SurrogateArgs& s, cudaStream_t st);
 cudaError_t launch_pack_mlp(const float* params, const float* norm, MlpDev* out, cudaStream_t s);
 cudaError_t launch_mlp_eval(const MlpDev* w, const float* X, long long n, float* Y, cudaStream_t s);
+cudaError_t launch_mlp_targets(const ChemArgs& c, const float* x1, const float* T1, float* Y, cudaStream_t s);
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s);

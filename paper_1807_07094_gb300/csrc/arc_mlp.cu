@@ -216,15 +216,6 @@ __global__ void k_features(const float* nH, const float* xHI, const float* xHeI,
     }
 }
 
-// raw targets: changes of the three fractions and log10 of the temperature ratio
-__global__ void k_targets(const float* x0, const float* x1, const float* T0, const float* T1, long long n, float* Y) {
-    // x0, x1: 3 x n fractions (HI, HeI, HeII) before and after
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        for (int q = 0; q < 3; ++q) Y[i * MLP_OUT + q] = x1[q * n + i] - x0[q * n + i];
-        Y[i * MLP_OUT + 3] = log10f(T1[i] / T0[i]);
-    }
-}
-
 int nblk(long long n, int t = 256) {
     long long b = (n + t - 1) / t;
     if (b > 152 * 8) b = 152 * 8;
@@ -457,13 +448,6 @@ arc_status arc_mlp_features(const float* nH, const float* xHI, const float* xHeI
                             void* stream) {
     if (!nH || !xHI || !xHeI || !xHeII || !T || !gamma || !heat || !X || n < 0 || !(dt > 0)) return ARC_E_INVALID;
     k_features<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(nH, xHI, xHeI, xHeII, T, gamma, heat, log10f((float)dt), n, X);
-    return cudaGetLastError() == cudaSuccess ? ARC_OK : ARC_E_CUDA;
-}
-
-arc_status arc_mlp_targets(const float* x0, const float* x1, const float* T0, const float* T1, long long n, float* Y,
-                           void* stream) {
-    if (!x0 || !x1 || !T0 || !T1 || !Y || n < 0) return ARC_E_INVALID;
-    k_targets<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(x0, x1, T0, T1, n, Y);
     return cudaGetLastError() == cudaSuccess ? ARC_OK : ARC_E_CUDA;
 }
 
