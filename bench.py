@@ -163,6 +163,20 @@ def cpu_baseline(w, budget_s: float = 15.0):
                       f"256^3 field in its initial state: {segs} segments in {dt:.1f} s CPU"}
 
 
+def reduce_over_ranks(work, ms, world: int, device: str = "cpu"):
+    """Whole-job aggregate of the replicas: total work over all ranks and the
+    slowest rank's time (the job ends when the last rank ends)."""
+    if world <= 1:
+        return float(work), float(ms)
+    import torch
+    import torch.distributed as dist
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(w.item()), float(t.item())
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -306,15 +320,10 @@ def run_ours(args):
     segs_e2e = a.stats()["segments_total"] - segs_e0
     a.close()
 
-    # max over ranks of the timed region, sum of work
-    tot_segs, max_ms = float(segs), ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([float(segs), ms], dtype=torch.float64, device="cuda")
-        s = tt.clone()
-        dist.all_reduce(s[:1], op=dist.ReduceOp.SUM)
-        dist.all_reduce(s[1:], op=dist.ReduceOp.MAX)
-        tot_segs, max_ms = float(s[0]), float(s[1])
+    # max over ranks of the timed region, sum of work (replicas: weak scaling)
+    dev = "cuda" if world > 1 and torch.distributed.get_backend() == "nccl" else "cpu"
+    tot_segs, max_ms = reduce_over_ranks(segs, ms, world, dev)
+    tot_e2e, max_e2e = reduce_over_ranks(segs_e2e, t_e2e * 1e3, world, dev)
     if rank != 0:
         return 0
     value = tot_segs / (max_ms / 1e3)
@@ -341,7 +350,7 @@ def run_ours(args):
                      "traffic": (traffic_per_seg * sum(trace_segs) / len(trace_segs)) if traffic_per_seg else None,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if pk else "fallback 6.8 TB/s",
                      "kernel": "k_trace", "algo_bytes_per_segment": ALGO_BYTES_PER_SEGMENT},
-        "e2e": {"value": segs_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * 4 * n3,
+        "e2e": {"value": tot_e2e / (max_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": 5 * 4 * n3,
                 "d2h_bytes_per_step": 4 * 4 * n3},
         "surrogate": surrogate,
         "gpu_launches": 6 * args.steps,
