@@ -234,7 +234,7 @@ arc_status arc_get_tuning(arc_ctx* ctx, int* block_threads, int* blocks_per_sm, 
  *   budget          NULL or host double[4], as for arc_trace
  *   stream          cudaStream_t for the work (NULL = legacy default stream)
  *
- * Scratch memory is one fixed file-scope device array of about 22 MB that every
+ * Scratch memory is one fixed file-scope device array of about 18 MB that every
  * device which loads libarc holds until the process exits.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the array and it

@@ -31,6 +31,7 @@ struct Scalars {
     unsigned int heartbeat;
     unsigned int pad0;
     double escaped;
+    double rounding;
     unsigned long long counters[CNT_ALL];
     unsigned long long nrec;
     double budget_out[2];
@@ -58,8 +59,7 @@ struct arc_ctx {
     // fields (C order)
     float *nH = nullptr, *xHI = nullptr, *xHeI = nullptr, *xHeII = nullptr, *T = nullptr;
     // internal brick layout
-    float4* kappa = nullptr;
-    float4* acc = nullptr;
+    float4* rec = nullptr;     // cell records: optical depth, absorbed photons (32 B per cell)
     float *gamma = nullptr, *heat = nullptr;
     // sources
     std::vector<HostSource> hsrc;
@@ -252,8 +252,8 @@ TraceArgs trace_args(arc_ctx* c) {
     a.ng = c->p.ngroups;
     a.l_base = c->p.l_base;
     a.l_max = c->p.l_max;
-    a.kappa = c->kappa;
-    a.acc = c->acc;
+    a.kappa = c->rec;
+    a.acc = c->rec;
     a.src = c->dsrc;
     a.nsrc = c->nsrc_dev;
     for (int l = 0; l <= ARC_MAX_LEVEL; ++l) a.rsplit[l] = c->rsplit[l];
@@ -270,6 +270,7 @@ TraceArgs trace_args(arc_ctx* c) {
     a.status = &c->scal->status;
     a.heartbeat = &c->scal->heartbeat;
     a.escaped = &c->scal->escaped;
+    a.rounding = &c->scal->rounding;
     a.counters = c->scal->counters;
     a.recs = c->recs;
     a.nrec = &c->scal->nrec;
@@ -310,8 +311,7 @@ arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
     for (int s = 0; s < 3; ++s)
         for (int b = 0; b < ARC_MAX_GROUPS; ++b)
             P.sig_dx[s][b] = (b < c->p.ngroups) ? (float)(c->p.sigma[s][b] * c->dx) : 0.f;
-    P.kappa = c->kappa;
-    P.acc = c->acc;
+    P.rec = c->rec;
     CK(launch_prep(P, c->stream));
     TraceArgs A = trace_args(c);
     if (seeds_limit > 0 && seeds_limit < A.nseeds) A.nseeds = seeds_limit;
@@ -337,12 +337,13 @@ arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
             F.egap_erg[s][b] = on ? (float)((c->p.E_group_eV[b] - E_S[s]) * EV_ERG) : 0.f;
         }
     F.scale = (float)(PHOT_UNIT / (c->dx * c->dx * c->dx));
-    F.acc = c->acc;
+    F.rec = c->rec;
     F.gamma = c->gamma;
     F.heat = c->heat;
     F.absorbed_part = c->absorbed_part;
     CK(launch_finalize(F, c->nparts, c->stream));
-    CK(launch_budget(c->absorbed_part, c->nparts, &c->scal->escaped, c->scal->budget_out, c->stream));
+    CK(launch_budget(c->absorbed_part, c->nparts, &c->scal->escaped, &c->scal->rounding, c->scal->budget_out,
+                     c->stream));
     return ARC_OK;
 }
 
@@ -447,8 +448,7 @@ arc_status arc_create(arc_ctx** out, const arc_grid* g, const arc_params* p, voi
     e = e ? e : dalloc(&c->xHeI, n3);
     e = e ? e : dalloc(&c->xHeII, n3);
     e = e ? e : dalloc(&c->T, n3);
-    e = e ? e : dalloc(&c->kappa, nbc);
-    e = e ? e : dalloc(&c->acc, 2 * nbc);
+    e = e ? e : dalloc(&c->rec, 2 * nbc);
     e = e ? e : dalloc(&c->gamma, 3 * n3);
     e = e ? e : dalloc(&c->heat, 3 * n3);
     c->qcap = 1ull << 22;
@@ -803,7 +803,7 @@ void arc_destroy(arc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (int i = 0; i < 4; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-    void* ptrs[] = {c->nH, c->xHI, c->xHeI, c->xHeII, c->T, c->kappa, c->acc, c->gamma, c->heat,
+    void* ptrs[] = {c->nH, c->xHI, c->xHeI, c->xHeII, c->T, c->rec, c->gamma, c->heat,
                     c->dsrc, c->seeds, c->qdata, c->qseq, c->scal, c->absorbed_part, c->mlp, c->fb_list};
     for (void* q : ptrs) dfree(q);
     if (c->own_stream) cudaStreamDestroy(c->stream);

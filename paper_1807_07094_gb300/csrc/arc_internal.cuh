@@ -82,8 +82,11 @@ struct __align__(16) SourceDev {
 // Arguments of the tracer kernels.
 struct TraceArgs {
     int n, nb, ng, l_base, l_max;
-    const float4* kappa;      // [brick cells] optical depth per cell length, per group
-    float4* acc;              // [2*brick cells] photons absorbed per group: hi, lo pairs
+    // cell records [2 * brick cells]: [2q] optical depth per cell length per
+    // group, [2q + 1] photons absorbed per group (FP32 sums); kappa and acc
+    // both point at the record array
+    const float4* kappa;
+    float4* acc;
     const SourceDev* src;
     int nsrc;
     float rsplit[ARC_MAX_LEVEL + 1];   // split distance per level [cells]
@@ -103,6 +106,7 @@ struct TraceArgs {
     unsigned int* status;     // device status word (ERR_*)
     unsigned int* heartbeat;  // progress counter for the idle-wait bound
     double* escaped;          // photons that left the box [PHOT_UNIT]
+    double* rounding;         // photons the FP32 cell sums rounded away [PHOT_UNIT]
     unsigned long long* counters;  // segments, rays, splits, terminated, escaped, donations, maxlevel
     arc_ray_rec* recs;
     unsigned long long* nrec;
@@ -125,8 +129,7 @@ struct PrepArgs {
     const float* xHeII;
     float y;                  // n_He / n_H
     float sig_dx[3][ARC_MAX_GROUPS];   // sigma_{s,b} * dx [cm^3]: kappa = sum_s sig_dx n_s
-    float4* kappa;
-    float4* acc;
+    float4* rec;              // cell records (optical depth, absorbed photons)
 };
 struct FinalizeArgs {
     int n, nb, ng;
@@ -138,7 +141,7 @@ struct FinalizeArgs {
     float sig[3][ARC_MAX_GROUPS];      // sigma_{s,b} [cm^2]
     float egap_erg[3][ARC_MAX_GROUPS]; // (E_b - E_s) [erg]
     float scale;              // PHOT_UNIT / V [1/(s cm^3)]
-    const float4* acc;
+    const float4* rec;        // cell records: absorbed photons at [2q + 1]
     float* gamma;             // 3*n^3
     float* heat;              // 3*n^3
     double* absorbed_part;    // per block FP64 partial of absorbed photons [PHOT_UNIT]
@@ -240,7 +243,7 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_budget(const double* part, int nparts, const double* escaped, double* out,
+cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding, double* out,
                           cudaStream_t s);
 cudaError_t launch_validate(const float* nH, const float* xHI, const float* xHeI,
                             const float* xHeII, const float* T, long long ncell,

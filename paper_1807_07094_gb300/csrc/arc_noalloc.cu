@@ -42,6 +42,7 @@ struct NaScalars {
     unsigned int status;
     unsigned int heartbeat;
     double escaped;
+    double rounding;
     unsigned long long counters[CNT_ALL];
     unsigned long long nrec;
     double budget_out[2];
@@ -49,9 +50,8 @@ struct NaScalars {
 
 // byte offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t OFF_KAPPA = 0;
-constexpr size_t OFF_ACC = al(OFF_KAPPA + NA_CELLS * sizeof(float4));
-constexpr size_t OFF_QDATA = al(OFF_ACC + 2 * NA_CELLS * sizeof(float4));
+constexpr size_t OFF_REC = 0;   // cell records: optical depth, absorbed photons
+constexpr size_t OFF_QDATA = al(OFF_REC + 2 * NA_CELLS * sizeof(float4));
 constexpr size_t OFF_QSEQ = al(OFF_QDATA + NA_QCAP * sizeof(Entry));
 constexpr size_t OFF_SEEDS = al(OFF_QSEQ + NA_QCAP * sizeof(unsigned long long));
 constexpr size_t OFF_SRC = al(OFF_SEEDS + (size_t)NA_MAX_SEEDS * sizeof(Entry));
@@ -59,7 +59,7 @@ constexpr size_t OFF_PARTS = al(OFF_SRC + (size_t)NA_MAX_SRC * sizeof(SourceDev)
 constexpr size_t OFF_SCAL = al(OFF_PARTS + NA_NPARTS * sizeof(double));
 constexpr size_t NA_BYTES = al(OFF_SCAL + sizeof(NaScalars));
 
-// The scratch: file scope, fixed size (about 22 MB), held by every device
+// The scratch: file scope, fixed size (about 18 MB), held by every device
 // that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -96,8 +96,7 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
         g_scratch_addr[dev] = (unsigned char*)ptr;
     }
     unsigned char* base = g_scratch_addr[dev];
-    float4* kappa = (float4*)(base + OFF_KAPPA);
-    float4* acc = (float4*)(base + OFF_ACC);
+    float4* rec = (float4*)(base + OFF_REC);
     Entry* qdata = (Entry*)(base + OFF_QDATA);
     unsigned long long* qseq = (unsigned long long*)(base + OFF_QSEQ);
     Entry* seeds = (Entry*)(base + OFF_SEEDS);
@@ -180,8 +179,7 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     for (int sp = 0; sp < 3; ++sp)
         for (int b = 0; b < ARC_MAX_GROUPS; ++b)
             P.sig_dx[sp][b] = (b < G) ? (float)(p->sigma[sp][b] * dx) : 0.f;
-    P.kappa = kappa;
-    P.acc = acc;
+    P.rec = rec;
     NA_CK(launch_prep(P, s));
 
     TraceArgs A;
@@ -191,8 +189,8 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     A.ng = G;
     A.l_base = p->l_base;
     A.l_max = p->l_max;
-    A.kappa = kappa;
-    A.acc = acc;
+    A.kappa = rec;
+    A.acc = rec;
     A.src = dsrc;
     A.nsrc = ns;
     for (int l = 0; l <= ARC_MAX_LEVEL; ++l) A.rsplit[l] = (float)na_r_split(p->phi, l);
@@ -209,6 +207,7 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     A.status = &scal->status;
     A.heartbeat = &scal->heartbeat;
     A.escaped = &scal->escaped;
+    A.rounding = &scal->rounding;
     A.counters = scal->counters;
     A.recs = nullptr;
     A.nrec = &scal->nrec;
@@ -246,12 +245,12 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
             F.egap_erg[sp][b] = on ? (float)((p->E_group_eV[b] - E_S[sp]) * EV_ERG) : 0.f;
         }
     F.scale = (float)(PHOT_UNIT / (dx * dx * dx));
-    F.acc = acc;
+    F.rec = rec;
     F.gamma = gamma;
     F.heat = heat;
     F.absorbed_part = parts;
     NA_CK(launch_finalize(F, NA_NPARTS, s));
-    NA_CK(launch_budget(parts, NA_NPARTS, &scal->escaped, scal->budget_out, s));
+    NA_CK(launch_budget(parts, NA_NPARTS, &scal->escaped, &scal->rounding, scal->budget_out, s));
 
     // the source table was copied from this stack frame: wait before returning
     NaScalars S;

@@ -27,8 +27,11 @@
 //   k_finalize instead of per segment;
 // * photon conservation is exact by construction: each segment moves exactly
 //   D = N_before - N_after from the ray into the cell (Sterbenz-exact FP32
-//   subtraction) and the cell sums are compensated (TwoSum on the value the
-//   atomic returns, error added to a second word).
+//   subtraction); the cell sums are FP32 and the rounding error of every
+//   addition (TwoSum on the value the atomic returns) goes to an FP64 ledger;
+// * a cell's record is one 32-byte sector: its optical depth per cell length
+//   (read) followed by its absorbed photons (atomically added), so the read
+//   brings into L2 the sector the atomic then updates.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -146,19 +149,20 @@ __device__ __forceinline__ void fold_low(float& Nh, float& Nl, float lo) {
     Nh = s;
 }
 
-// compensated vector deposit of D = d + e into a cell's (hi, lo) accumulator
-// pair: the atomic returns the old hi, the rounding error of old + d plus e
-// goes to lo.
+// Vector deposit of D = d + e into a cell's FP32 accumulator: the atomic
+// returns the old value, from which the rounding error of old + d is
+// recovered exactly (TwoSum); that error plus e, the part of the deposit below
+// d's precision, is returned for the caller's rounding ledger.  The cell sums
+// are then plain FP32 (relative error ~1e-7, far below the rates' needs) while
+// the photon budget, cells plus ledger plus escapes, stays exact.
 template <int NG>
-__device__ __forceinline__ void deposit(float4* acc, uint64_t idx, float4 d, float4 e) {
-    float4* hi = acc + 2 * idx;
-    const float4 old = atom_add_v4(hi, d);
-    float4 l;
-    l.x = __fadd_rn(two_sum_err(old.x, d.x), e.x);
-    l.y = NG > 1 ? __fadd_rn(two_sum_err(old.y, d.y), e.y) : 0.f;   // unused groups stay zero
-    l.z = NG > 2 ? __fadd_rn(two_sum_err(old.z, d.z), e.z) : 0.f;
-    l.w = NG > 3 ? __fadd_rn(two_sum_err(old.w, d.w), e.w) : 0.f;
-    if (l.x != 0.f || l.y != 0.f || l.z != 0.f || l.w != 0.f) red_add_v4(hi + 1, l);
+__device__ __forceinline__ float deposit(float4* rec, uint64_t idx, float4 d, float4 e) {
+    const float4 old = atom_add_v4(rec + 2 * idx + 1, d);
+    float err = __fadd_rn(two_sum_err(old.x, d.x), e.x);
+    if (NG > 1) err = __fadd_rn(err, __fadd_rn(two_sum_err(old.y, d.y), e.y));
+    if (NG > 2) err = __fadd_rn(err, __fadd_rn(two_sum_err(old.z, d.z), e.z));
+    if (NG > 3) err = __fadd_rn(err, __fadd_rn(two_sum_err(old.w, d.w), e.w));
+    return err;
 }
 
 // ------------------------------------------------------------------ HEALPix
@@ -362,7 +366,7 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
     R.ty = (u.y != 0.0f) ? next_plane_t(R.cy, R.oy, R.iy) : INFINITY;
     R.tz = (u.z != 0.0f) ? next_plane_t(R.cz, R.oz, R.iz) : INFINITY;
     R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
-    R.kap = ldg_f4(&A.kappa[R.idx]);
+    R.kap = ldg_f4(&A.kappa[2 * R.idx]);
     return EV_NONE;
 }
 
@@ -371,7 +375,7 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
 // next cell's record is loaded before the current cell's deposit is issued, so
 // the load and the atomic round trip overlap.
 template <int NG>
-__device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
+__device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) {
     const float t = fminf(R.tx, fminf(R.ty, R.tz));
     const bool split = R.rstop <= t;
     const float r1 = split ? R.rstop : t;
@@ -420,12 +424,12 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R) {
             ev = EV_ESC;
         } else {
             R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
-            R.kap = ldg_f4(&A.kappa[R.idx]);
+            R.kap = ldg_f4(&A.kappa[2 * R.idx]);
         }
     }
     if (D.x != 0.f || D.y != 0.f || D.z != 0.f || D.w != 0.f || E.x != 0.f || E.y != 0.f ||
         E.z != 0.f || E.w != 0.f)
-        deposit<NG>(A.acc, idx, D, E);
+        rerr = __fadd_rn(rerr, deposit<NG>(A.acc, idx, D, E));
     return ev;
 }
 
@@ -452,6 +456,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
     unsigned nseg = 0, nrays = 0, nsplit = 0, nterm = 0, nesc = 0, ndon = 0;   // per lane
     unsigned maxlev = 0;
     double esc_photons = 0.0;
+    double rounding = 0.0;             // photons the FP32 cell sums rounded away (exact)
     unsigned round = 0;
 
     Ray R;
@@ -597,12 +602,14 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
 
         // ------------------------------------------------------------ trace
         if (active && ev == EV_NONE) {
+            float rerr = 0.0f;   // rounding ledger of this batch (a few ulps of its deposits)
 #pragma unroll 1
             for (int it = 0; it < SEG_BATCH; ++it) {
-                ev = segment<NG>(A, R);
+                ev = segment<NG>(A, R, rerr);
                 nseg++;
                 if (ev != EV_NONE) break;
             }
+            rounding += (double)rerr;
         }
 
         // ------------------------------------------------------------ events
@@ -716,6 +723,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
         nterm += __shfl_down_sync(FULL, nterm, o);
         nesc += __shfl_down_sync(FULL, nesc, o);
         esc_photons += __shfl_down_sync(FULL, esc_photons, o);
+        rounding += __shfl_down_sync(FULL, rounding, o);
         maxlev = max(maxlev, __shfl_down_sync(FULL, maxlev, o));
     }
     if (lane == 0) {
@@ -728,6 +736,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
         atomicAdd(&A.counters[CNT_DONATE], (unsigned long long)ndon);
         atomicMax(&A.counters[CNT_MAXLEVEL], (unsigned long long)maxlev);
         if (esc_photons != 0.0) atomicAdd(A.escaped, esc_photons);
+        if (rounding != 0.0) atomicAdd(A.rounding, rounding);
     }
 }
 
@@ -756,9 +765,8 @@ __global__ void k_prep(const PrepArgs P) {
                 kb[g] = (g < P.ng) ? (P.sig_dx[0][g] * n0 + P.sig_dx[1][g] * n1 + P.sig_dx[2][g] * n2) : 0.f;
             kap = make_float4(kb[0], kb[1], kb[2], kb[3]);
         }
-        P.kappa[q] = kap;
-        P.acc[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P.acc[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.rec[2 * q] = kap;
+        P.rec[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -802,6 +810,7 @@ __global__ void k_reset(TraceArgs A, unsigned long long qcap, int nseeds) {
         *A.n_idle = 0;
         *A.heartbeat = 0;
         *A.escaped = 0.0;
+        *A.rounding = 0.0;
         for (int i = 0; i < CNT_N; ++i) A.counters[i] = 0;
         A.counters[CNT_TRACES_TOTAL] += 1;
         if (A.nrec) *A.nrec = 0;
@@ -810,7 +819,7 @@ __global__ void k_reset(TraceArgs A, unsigned long long qcap, int nseeds) {
 }
 
 // ------------------------------------------------------------------ finalize
-// Per cell: D_b photons absorbed in group b (compensated sum).  Eq. (ion)
+// Per cell: D_b photons absorbed in group b (FP32 sum).  Eq. (ion)
 // splits D_b over the absorbers in proportion to sigma_{s,b} n_s and divides
 // by V n_s; with kappa_b = sum_s sigma_{s,b} n_s this is
 //   Gamma_s = (PHOT_UNIT / V) sum_b D_b sigma_{s,b} / kappa_b,
@@ -824,10 +833,9 @@ __global__ void k_finalize(const FinalizeArgs F) {
         const int j = (int)((c / F.n) % F.n);
         const int i = (int)(c / ((uint64_t)F.n * F.n));
         const uint64_t q = brick_index(i, j, k, F.nb);
-        const float4 hi = F.acc[2 * q], lo = F.acc[2 * q + 1];
-        part += ((double)hi.x + (double)lo.x) + ((double)hi.y + (double)lo.y) +
-                ((double)hi.z + (double)lo.z) + ((double)hi.w + (double)lo.w);
-        const float D[4] = {hi.x + lo.x, hi.y + lo.y, hi.z + lo.z, hi.w + lo.w};
+        const float4 a = F.rec[2 * q + 1];
+        part += ((double)a.x + (double)a.y) + ((double)a.z + (double)a.w);
+        const float D[4] = {a.x, a.y, a.z, a.w};
         const float nh = F.nH[c];
         const float ns[3] = {nh * F.xHI[c], F.y * nh * F.xHeI[c], F.y * nh * F.xHeII[c]};
         float g[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
@@ -862,7 +870,8 @@ __global__ void k_finalize(const FinalizeArgs F) {
     }
 }
 
-__global__ void k_budget(const double* part, int nparts, const double* escaped, double* out) {
+__global__ void k_budget(const double* part, int nparts, const double* escaped, const double* rounding,
+                         double* out) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
@@ -872,7 +881,7 @@ __global__ void k_budget(const double* part, int nparts, const double* escaped, 
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        out[0] = t;
+        out[0] = t + *rounding;   // the cell sums plus what their FP32 additions rounded away
         out[1] = *escaped;
     }
 }
@@ -925,9 +934,9 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s) {
     k_finalize<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_budget(const double* part, int nparts, const double* escaped, double* out,
+cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding, double* out,
                           cudaStream_t s) {
-    k_budget<<<1, 256, 0, s>>>(part, nparts, escaped, out);
+    k_budget<<<1, 256, 0, s>>>(part, nparts, escaped, rounding, out);
     return cudaGetLastError();
 }
 
