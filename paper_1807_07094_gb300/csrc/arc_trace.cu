@@ -85,10 +85,6 @@ __device__ __forceinline__ float4 atom_add_v4(float4* a, float4 v) {
                  : "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
     return o;
 }
-__device__ __forceinline__ void red_add_v4(float4* a, float4 v) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(a), "f"(v.x), "f"(v.y),
-                 "f"(v.z), "f"(v.w));
-}
 __device__ __forceinline__ float4 ldg_f4(const float4* p) { return __ldg(p); }
 
 // rounding error of a + b (Knuth TwoSum, round-to-nearest throughout)
@@ -395,8 +391,8 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
     const bool term = sumN < R.thr;
     if (term) {
         // below threshold: every remaining photon stays in this cell
-        D = Nh0;
-        E = Nl0;
+        D = make_float4(Nh0.x, NG > 1 ? Nh0.y : 0.f, NG > 2 ? Nh0.z : 0.f, NG > 3 ? Nh0.w : 0.f);
+        E = make_float4(Nl0.x, NG > 1 ? Nl0.y : 0.f, NG > 2 ? Nl0.z : 0.f, NG > 3 ? Nl0.w : 0.f);
         R.N = make_float4(0.f, 0.f, 0.f, 0.f);
         R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -433,12 +429,21 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
     return ev;
 }
 
+// per-warp tallies of one launch (shared memory)
+struct WarpTally {
+    unsigned long long nrays, nsplit, nterm, nesc, ndon;
+    double esc;                // photons that left the box
+    long long live_delta;      // rays created minus finished, not yet flushed
+    unsigned maxlev;
+};
+
 constexpr int SEG_BATCH = 4;          // segments per lane between warp event rounds
 constexpr int HEARTBEAT_EVERY = 1024; // event rounds between progress signals
 
 #ifndef ARC_TRACE_MIN_BLOCKS
-#define ARC_TRACE_MIN_BLOCKS 2   // resident 256-thread blocks per SM the registers must allow
-                                 // (2: no spills; measured faster than 3 or 4 with spills)
+#define ARC_TRACE_MIN_BLOCKS 3   // resident 256-thread blocks per SM the registers must allow
+                                 // (3: 80 registers, 24 warps/SM; measured 16 % faster than 2
+                                 // blocks without spills, and faster than 4)
 #endif
 template <int NG>
 __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const TraceArgs A) {
@@ -452,10 +457,13 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
 
     // deque [bot, top) of pending work items, indices modulo cap (warp-uniform)
     unsigned bot = 0, top = 0;
-    long long live_delta = 0;          // lane 0 only: rays created minus finished, not yet flushed
-    unsigned nseg = 0, nrays = 0, nsplit = 0, nterm = 0, nesc = 0, ndon = 0;   // per lane
-    unsigned maxlev = 0;
-    double esc_photons = 0.0;
+    // per-warp tallies live in shared memory (written by lane 0, escapes by
+    // shared FP64 atomics) so that they do not hold registers in every lane
+    __shared__ WarpTally tally_all[8];
+    WarpTally& W = tally_all[wib];
+    if (lane == 0) W = WarpTally{};
+    __syncwarp();
+    unsigned nseg = 0;                 // per lane
     double rounding = 0.0;             // photons the FP32 cell sums rounded away (exact)
     unsigned round = 0;
 
@@ -464,9 +472,9 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
     int ev = EV_NONE;
 
     auto flush_live = [&]() {
-        if (lane == 0 && live_delta != 0) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(A.live), (unsigned long long)live_delta);
-            live_delta = 0;
+        if (lane == 0 && W.live_delta != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(A.live), (unsigned long long)W.live_delta);
+            W.live_delta = 0;
         }
     };
     // move the oldest `cnt` items of the deque to the global ring (all lanes)
@@ -480,7 +488,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
             __syncwarp();
             if (!q_push_warp(A, e, chunk, lane, mandatory)) break;   // not pushed: keep them here
             bot += chunk;
-            ndon += chunk;
+            if (lane == 0) W.ndon += chunk;
             cnt -= chunk;
         }
     };
@@ -585,8 +593,10 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                 if (mine) {
                     ev = start_ray(A, e, k0 + rank, R);
                     active = true;
-                    nrays++;
-                    maxlev = max(maxlev, (unsigned)R.level);
+                }
+                if (lane == 0) {
+                    W.nrays += (unsigned)__popc(taken);
+                    W.maxlev = max(W.maxlev, (unsigned)key_level(e.key));
                 }
                 idle &= ~taken;
                 __syncwarp();
@@ -641,18 +651,25 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
             const bool is_split = has_ev && ev == EV_SPLIT;
             if (has_ev && !is_split) {
                 if (ev == EV_ESC) {
-                    esc_photons += ((double)R.N.x + (double)R.Nl.x) + ((double)R.N.y + (double)R.Nl.y) +
-                                   ((double)R.N.z + (double)R.Nl.z) + ((double)R.N.w + (double)R.Nl.w);
-                    nesc++;
-                } else {
-                    nterm++;
+                    atomicAdd(&W.esc, ((double)R.N.x + (double)R.Nl.x) + ((double)R.N.y + (double)R.Nl.y) +
+                                          ((double)R.N.z + (double)R.Nl.z) +
+                                          (NG > 3 ? ((double)R.N.w + (double)R.Nl.w) : 0.0));
                 }
+            }
+            const unsigned escm = __ballot_sync(FULL, has_ev && !is_split && ev == EV_ESC);
+            if (has_ev && !is_split) {
                 active = false;
                 ev = EV_NONE;
             }
             const unsigned sm = __ballot_sync(FULL, is_split);
             const unsigned em = evm & ~sm;
-            if (lane == 0) live_delta += 3 * (long long)__popc(sm) - (long long)__popc(em);
+            if (lane == 0) {
+                W.live_delta += 3 * (long long)__popc(sm) - (long long)__popc(em);
+                W.nesc += (unsigned)__popc(escm);
+                W.nterm += (unsigned)__popc(em & ~escm);
+                W.nsplit += (unsigned)__popc(sm);
+                W.nrays += (unsigned)__popc(sm);
+            }
             if (sm) {
                 // make room: donate the oldest items if this round's pushes would not fit
                 const unsigned need = (unsigned)__popc(sm);
@@ -660,7 +677,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                 const bool room = top - bot + need <= cap;
                 if (!room && lane == 0) {
                     // ring and deque both full: these siblings are lost (flagged)
-                    live_delta -= 3 * (long long)need;
+                    W.live_delta -= 3 * (long long)need;
                     atomicOr(A.status, ERR_QUEUE_FULL);
                 }
                 if (is_split) {
@@ -672,7 +689,6 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                     e.N = make_float4(R.N.x * 0.25f, NG > 1 ? R.N.y * 0.25f : 0.f,
                                       NG > 2 ? R.N.z * 0.25f : 0.f, NG > 3 ? R.N.w * 0.25f : 0.f);
                     if (room) stack[(top + __popc(sm & lt_mask)) & cmask] = e;
-                    nsplit++;
                     // children 1..3 carry exact FP32 quarters; child 0 (this lane)
                     // also inherits the parent's sub-ulp low part, so no photon
                     // is lost and no cell receives a spurious deposit
@@ -681,9 +697,11 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                     fold_low(R.N.x, R.Nl.x, keep.x);
                     fold_low(R.N.y, R.Nl.y, keep.y);
                     fold_low(R.N.z, R.Nl.z, keep.z);
-                    fold_low(R.N.w, R.Nl.w, keep.w);
-                    nrays++;
-                    maxlev = max(maxlev, (unsigned)R.level);
+                    if (NG > 3) fold_low(R.N.w, R.Nl.w, keep.w);
+                }
+                {
+                    const unsigned lv = __reduce_max_sync(FULL, is_split ? (unsigned)R.level : 0u);
+                    if (lane == 0) W.maxlev = max(W.maxlev, lv);
                 }
                 __syncwarp();
                 if (room) top += need;
@@ -718,24 +736,19 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
     unsigned long long wseg = nseg;
     for (int o = 16; o > 0; o >>= 1) {
         wseg += __shfl_down_sync(FULL, wseg, o);
-        nrays += __shfl_down_sync(FULL, nrays, o);
-        nsplit += __shfl_down_sync(FULL, nsplit, o);
-        nterm += __shfl_down_sync(FULL, nterm, o);
-        nesc += __shfl_down_sync(FULL, nesc, o);
-        esc_photons += __shfl_down_sync(FULL, esc_photons, o);
         rounding += __shfl_down_sync(FULL, rounding, o);
-        maxlev = max(maxlev, __shfl_down_sync(FULL, maxlev, o));
     }
+    __syncwarp();
     if (lane == 0) {
         atomicAdd(&A.counters[CNT_SEG], wseg);
         atomicAdd(&A.counters[CNT_SEG_TOTAL], wseg);
-        atomicAdd(&A.counters[CNT_RAYS], (unsigned long long)nrays);
-        atomicAdd(&A.counters[CNT_SPLIT], (unsigned long long)nsplit);
-        atomicAdd(&A.counters[CNT_TERM], (unsigned long long)nterm);
-        atomicAdd(&A.counters[CNT_ESC], (unsigned long long)nesc);
-        atomicAdd(&A.counters[CNT_DONATE], (unsigned long long)ndon);
-        atomicMax(&A.counters[CNT_MAXLEVEL], (unsigned long long)maxlev);
-        if (esc_photons != 0.0) atomicAdd(A.escaped, esc_photons);
+        atomicAdd(&A.counters[CNT_RAYS], W.nrays);
+        atomicAdd(&A.counters[CNT_SPLIT], W.nsplit);
+        atomicAdd(&A.counters[CNT_TERM], W.nterm);
+        atomicAdd(&A.counters[CNT_ESC], W.nesc);
+        atomicAdd(&A.counters[CNT_DONATE], W.ndon);
+        atomicMax(&A.counters[CNT_MAXLEVEL], (unsigned long long)W.maxlev);
+        if (W.esc != 0.0) atomicAdd(A.escaped, W.esc);
         if (rounding != 0.0) atomicAdd(A.rounding, rounding);
     }
 }
