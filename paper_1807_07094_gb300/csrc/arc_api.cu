@@ -434,9 +434,10 @@ arc_status arc_create(arc_ctx** out, const arc_grid* g, const arc_params* p, voi
     }
     // allow the largest tuning (256 threads x 256 deque entries) once, for every context
     for (int ng : {1, 3, 4})
-        if (cudaFuncSetAttribute(trace_kernel_ptr(ng), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 trace_smem_bytes(256, 8)) != cudaSuccess)
-            return bail(ARC_E_CUDA);
+        for (bool rec : {false, true})
+            if (cudaFuncSetAttribute(trace_kernel_ptr(ng, rec), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     trace_smem_bytes(256, 8)) != cudaSuccess)
+                return bail(ARC_E_CUDA);
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(ARC_E_CUDA);
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return bail(ARC_E_CUDA);

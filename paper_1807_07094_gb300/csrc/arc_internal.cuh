@@ -252,6 +252,6 @@ cudaError_t launch_make_seeds(const SourceDev* src, int nsrc, int l_base, Entry*
                               cudaStream_t s);
 cudaError_t launch_chem(const ChemArgs& a, cudaStream_t s);
 int trace_smem_bytes(int block, int stack_log2);
-const void* trace_kernel_ptr(int ng);
+const void* trace_kernel_ptr(int ng, bool rec = false);   // rec: the per-ray-record variant
 
 }  // namespace arc

@@ -370,7 +370,7 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
 // distance, Eq. (ion) absorption in each of the NG groups, then step.  The
 // next cell's record is loaded before the current cell's deposit is issued, so
 // the load and the atomic round trip overlap.
-template <int NG>
+template <int NG, bool REC>
 __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) {
     const float t = fminf(R.tx, fminf(R.ty, R.tz));
     const bool split = R.rstop <= t;
@@ -396,7 +396,7 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
         R.N = make_float4(0.f, 0.f, 0.f, 0.f);
         R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    R.visits++;
+    if (REC) R.visits++;   // per-ray records only
     R.r = r1;
     int ev = term ? EV_TERM : (split ? EV_SPLIT : EV_NONE);
     if (ev == EV_NONE) {
@@ -437,7 +437,13 @@ struct WarpTally {
     unsigned maxlev;
 };
 
-constexpr int SEG_BATCH = 4;          // segments per lane between warp event rounds
+#ifndef ARC_SEG_BATCH
+#define ARC_SEG_BATCH 16   // measured on the 256^3 field: 4 -> 53.7, 8 -> 56.9, 16 -> 57.6 Gsegments/s
+#endif
+#ifndef ARC_REFILL_IDLE
+#define ARC_REFILL_IDLE 16
+#endif
+constexpr int SEG_BATCH = ARC_SEG_BATCH;   // segments per lane between warp event rounds
 constexpr int HEARTBEAT_EVERY = 1024; // event rounds between progress signals
 
 #ifndef ARC_TRACE_MIN_BLOCKS
@@ -445,7 +451,7 @@ constexpr int HEARTBEAT_EVERY = 1024; // event rounds between progress signals
                                  // (3: 80 registers, 24 warps/SM; measured 16 % faster than 2
                                  // blocks without spills, and faster than 4)
 #endif
-template <int NG>
+template <int NG, bool REC>
 __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
         unsigned idle = __ballot_sync(FULL, !active);
         if (idle) {
             const int nidle = __popc(idle);
-            if (top == bot && (idle == FULL || (nidle >= 16 && (round & 3) == 0))) {
+            if (top == bot && (idle == FULL || (nidle >= ARC_REFILL_IDLE && (round & 3) == 0))) {
                 int got = acquire((nidle + 3) >> 2);
                 if (got == 0 && idle == FULL) {
                     // nothing anywhere for now: wait (bounded) for donations or the end
@@ -615,7 +621,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
             float rerr = 0.0f;   // rounding ledger of this batch (a few ulps of its deposits)
 #pragma unroll 1
             for (int it = 0; it < SEG_BATCH; ++it) {
-                ev = segment<NG>(A, R, rerr);
+                ev = segment<NG, REC>(A, R, rerr);
                 nseg++;
                 if (ev != EV_NONE) break;
             }
@@ -627,7 +633,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
         const unsigned evm = __ballot_sync(FULL, has_ev);
         if (evm) {
             // per-ray records (test aid)
-            if (A.recs != nullptr) {
+            if (REC && A.recs != nullptr) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(A.nrec, (unsigned long long)__popc(evm));
                 base = __shfl_sync(FULL, base, 0);
@@ -906,10 +912,15 @@ int trace_smem_bytes(int block, int stack_log2) {
     return (block / 32) * (1 << stack_log2) * (int)sizeof(Entry);
 }
 // the tracer is specialised on the number of frequency groups carried
-const void* trace_kernel_ptr(int ng) {
-    if (ng <= 1) return (const void*)k_trace<1>;
-    if (ng <= 3) return (const void*)k_trace<3>;
-    return (const void*)k_trace<4>;
+const void* trace_kernel_ptr(int ng, bool rec) {
+    if (rec) {
+        if (ng <= 1) return (const void*)k_trace<1, true>;
+        if (ng <= 3) return (const void*)k_trace<3, true>;
+        return (const void*)k_trace<4, true>;
+    }
+    if (ng <= 1) return (const void*)k_trace<1, false>;
+    if (ng <= 3) return (const void*)k_trace<3, false>;
+    return (const void*)k_trace<4, false>;
 }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
@@ -938,9 +949,15 @@ cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int n
 }
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s) {
     const int smem = trace_smem_bytes(block, a.stack_log2);
-    if (a.ng <= 1) k_trace<1><<<grid, block, smem, s>>>(a);
-    else if (a.ng <= 3) k_trace<3><<<grid, block, smem, s>>>(a);
-    else k_trace<4><<<grid, block, smem, s>>>(a);
+    if (a.recs != nullptr) {   // test aid: per-ray records (cell-visit counts)
+        if (a.ng <= 1) k_trace<1, true><<<grid, block, smem, s>>>(a);
+        else if (a.ng <= 3) k_trace<3, true><<<grid, block, smem, s>>>(a);
+        else k_trace<4, true><<<grid, block, smem, s>>>(a);
+    } else {
+        if (a.ng <= 1) k_trace<1, false><<<grid, block, smem, s>>>(a);
+        else if (a.ng <= 3) k_trace<3, false><<<grid, block, smem, s>>>(a);
+        else k_trace<4, false><<<grid, block, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s) {
