@@ -362,6 +362,20 @@ def run_ours(args):
     return 0
 
 
+def run_memops():
+    """Throughput ceilings of the tracer's per-segment memory pattern (random
+    32-byte cell records: 16-byte load, 16-byte vector atomic, both) on this
+    GPU; context for the roofline fraction."""
+    import paper_1807_07094_gb300.build as B
+    src = os.path.join(ROOT, "paper_1807_07094_gb300", "probe", "memops.cu")
+    exe = os.path.join(B.LIBDIR, "memops")
+    os.makedirs(B.LIBDIR, exist_ok=True)
+    subprocess.run([B.nvcc(), *B.ARCH, "-O3", "-o", exe, src], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    sys.stdout.write(r.stdout)
+    return r.returncode
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,9 +388,13 @@ def main():
                     help="profiling aid: trace only the first N sources of the workload")
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the e2e pass")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-ODE chemistry comparison")
+    ap.add_argument("--memops", action="store_true",
+                    help="measure the memory-operation ceilings of the tracer's access pattern and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.memops:
+        return run_memops()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
