@@ -48,6 +48,10 @@ MUTANTS = [
     ("case-B exponent", "return 2.753e-14 * pow(lam, 1.5)", "return 2.753e-14 * pow(lam, 1.4)"),
     ("limiter ignores n_HII", "const double lim = eps * fmax(fmin(nHI, nH - nHI), p->x_fp64 * nH);",
      "const double lim = eps * fmax(nHI, p->x_fp64 * nH);"),
+    ("negative-direction plane one cell off", "else if (u[a] < 0.0) tn[a] = ((double)cell[a] - o[a]) / u[a];",
+     "else if (u[a] < 0.0) tn[a] = ((double)cell[a] - 1.0 - o[a]) / u[a];"),
+    ("nearest plane picks the largest", "if (tn[2] < tn[ax]) ax = 2;", "if (tn[2] > tn[ax]) ax = 2;"),
+    ("segment from the cell start", "double ds = r1 - r;", "double ds = r1 - r0;"),
 ]
 
 # fast pins first; a mutant is killed at the first failure
@@ -60,6 +64,7 @@ PINS = [
     TR.test_clump_casts_sharp_shadow,
     TR.test_energy_budget_of_heating,
     lambda: TR.test_visit_counts_closed_form(0),
+    lambda: TR.test_cells_and_segments_against_plane_crossing_bruteforce((1.37, 2.11, 1.73)),
     CH.test_case_b_alpha_matches_paper_test1,
     lambda: CH.test_pure_h_equilibrium_quadratic(1e-3),
     lambda: CH.test_pure_h_equilibrium_quadratic(0.3),
