@@ -39,6 +39,9 @@ UNIT = "segments/s"
 WORKLOAD = ("cosmic_256: 256^3 lognormal n_H (sigma_ln 1.5, P(k)~k^-3, mean 2e-4), 1000 sources "
             "(cells ~ n_H^2, 1e48-1e51 ph/s log-uniform, 1e5 K blackbody in 3 groups), "
             "H+He, dt = 0.02 Myr, seed 1807")
+WORKLOAD_512 = ("cosmic_512: 512^3 lognormal n_H (sigma_ln 2.0, P(k)~k^-3, mean 2e-4), 10^4 sources "
+                "(cells ~ n_H^2, 1e47-1e51 ph/s log-uniform, 1e5 K blackbody in 3 groups), "
+                "H+He, dt = 0.02 Myr, seed 1807")
 # algorithmic bytes per ray-cell segment of the tracer (3 absorber densities
 # read + 6 per-absorber rates accumulated, FP32): 36 B
 ALGO_BYTES_PER_SEGMENT = 36
@@ -242,8 +245,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    w = W.cosmic_256()
-    if args.sources != w.nsrc:
+    w = W.cosmic_512() if args.workload == "cosmic_512" else W.cosmic_256()
+    if args.sources and args.sources < w.nsrc:
         # profiling aid: the same field with only the first N sources
         w = W.subset_sources(w, list(range(args.sources)))
     p = w.params()
@@ -335,8 +338,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (fields 5x64 MB, rates 6x64 MB, "
-                   "accumulators 512 MB per step)", "parallelism": "replicas" if world > 1 else "1 GPU",
+        "config": {"workload": WORKLOAD_512 if args.workload == "cosmic_512" else WORKLOAD,
+                   "l2": "inputs larger than L2 (fields 5 x n^3 x 4 B, rates 6 x n^3 x 4 B, cell records "
+                   "n^3 x 32 B per step)", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "trace_launch": {"block": tuning[0], "blocks_per_sm": tuning[1], "deque_entries": tuning[2],
                                     "chosen_by": "arc_autotune"}},
         "rt_step_ms": sum(trace_ms) / len(trace_ms), "trace_kernel_ms": trace_ms,
@@ -384,8 +388,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sources", type=int, default=1000,
+    ap.add_argument("--sources", type=int, default=0,
                     help="profiling aid: trace only the first N sources of the workload")
+    ap.add_argument("--workload", default="cosmic_256", choices=["cosmic_256", "cosmic_512"],
+                    help="cosmic_256 (256^3 x 1000 sources, the benchmark) or cosmic_512 (512^3 x 10^4)")
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the e2e pass")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-ODE chemistry comparison")
     ap.add_argument("--memops", action="store_true",

@@ -128,9 +128,11 @@ def compare_records(gpu_recs, orc_recs, n):
                 mismatches=mism, extra=extra, dup=dup, n_gpu=len(gpu_recs), n_orc=len(orc_recs))
 
 
-def rate_errors(g_gpu, g_orc, floor=GAMMA_FLOOR):
+def rate_errors(g_gpu, g_orc, floor=GAMMA_FLOOR, absorbers=None, min_photons=None):
     """Max relative error of the GPU rates over cells where the oracle exceeds
-    floor * max (per species)."""
+    floor * max (per species).  With absorbers (n_s V per species and cell)
+    and min_photons, only cells where species s absorbs more than min_photons
+    per second are compared (rate fields only; for heating the same cells)."""
     out = []
     for s in range(g_orc.shape[0]):
         o = g_orc[s]
@@ -139,6 +141,11 @@ def rate_errors(g_gpu, g_orc, floor=GAMMA_FLOOR):
             out.append((0.0, 0, float(np.abs(g_gpu[s]).max())))
             continue
         m = o > floor * mx
+        if absorbers is not None:
+            m &= absorbers[s] * o > min_photons
+        if not m.any():
+            out.append((0.0, 0, {}))
+            continue
         rel = np.abs(g_gpu[s][m] - o[m]) / o[m]
         i = int(np.argmax(rel))
         worst = dict(rel=float(rel[i]), orc_over_max=float(o[m][i] / mx), gpu=float(g_gpu[s][m][i]),

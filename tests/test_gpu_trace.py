@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 
 
 def check_pair(w, xs=(None, None, None), records=True, rtol=GAMMA_RTOL, max_inband_frac=0.05,
-               rates=True):
+               rates=True, flip_photons=None):
+    """flip_photons: compare rates only in cells where each species absorbs
+    more than 1e4 times this many photons per second (see the 512^3 test)."""
     g = gpu_trace(w, *xs, records=records)
     o = oracle_trace(w, *xs, records=records)
     launched, absorbed, escaped, emitted = g["budget"]
@@ -33,8 +35,21 @@ def check_pair(w, xs=(None, None, None), records=True, rtol=GAMMA_RTOL, max_inba
         # undecided decisions are rare (a guard against a band so wide that it
         # would hide real mismatches): at most 5 % of the rays by default
         assert c["undecided"] <= max_inband_frac * max(c["n_orc"], 1), c
+    ab = None
+    if flip_photons is not None:
+        y = w.Y / (4 * (1 - w.Y))
+        xHI, xHeI, xHeII = (w.xHI, w.xHeI, w.xHeII) if xs[0] is None else xs
+        V = (w.box_cm / w.n) ** 3
+        ab = np.stack([w.nH * xHI, y * w.nH * xHeI, y * w.nH * xHeII]).astype(np.float64) * V
+        # photons absorbed per second by each species, from the oracle's rates
     for name in (("gamma", "heat") if rates else ()):
-        errs = rate_errors(g[name], o[name])
+        if ab is not None:
+            Aphot = ab * o["gamma"]
+            errs = rate_errors(g[name], o[name], absorbers=Aphot / np.maximum(o[name], 1e-300),
+                               min_photons=1e4 * flip_photons)
+        else:
+            errs = rate_errors(g[name], o[name])
+        assert errs[0][1] > 0   # the comparison is never vacuous for HI
         for s, (rel, cnt, worst) in enumerate(errs):
             assert rel <= rtol, (name, s, cnt, worst, c if records else None)
     return g, o
@@ -159,6 +174,22 @@ def test_full_size_cosmic_256_sampled_sources(src):
     both sides (the whole 1000-source step is out of the oracle's reach)."""
     w = W.subset_sources(W.cosmic_256(), src)
     check_pair(w, records=True)
+
+
+def test_full_size_cosmic_512_sampled_source():
+    """The largest configuration (512^3, sigma_ln 2.0, 10^4 sources) at full
+    size, its faintest source traced by both sides: deep trees (levels up to
+    11) on a 0.5 GB-per-field grid."""
+    w = W.cosmic_512()
+    faintest = int(np.argmin(w.src_ndot.sum(1)))
+    ws = W.subset_sources(w, [faintest])
+    # Trees this deep terminate many rays near their photon threshold; a
+    # termination decided differently inside the decision band moves at most
+    # one threshold's worth of photons (term_frac times a level-1 ray's share)
+    # to the next cell.  Rates are compared where a species absorbs at least
+    # 1e4 times that, so that one such move stays within the 1e-4 bar.
+    thr = ws.params()["term_frac"] * ws.src_ndot.sum() / 48.0
+    check_pair(ws, records=True, flip_photons=thr)
 
 
 def test_autotune_picks_a_shape_and_keeps_results():
