@@ -33,7 +33,7 @@ class OrcParams(C.Structure):
         ("Y", C.c_double), ("phi", C.c_double), ("l_base", C.c_int), ("l_max", C.c_int),
         ("term_frac", C.c_double), ("eps_sub", C.c_double), ("x_fp64", C.c_double),
         ("isothermal", C.c_int), ("alpha_B_fixed", C.c_double), ("coll_ion", C.c_int),
-        ("z_compton", C.c_double),
+        ("z_compton", C.c_double), ("geo_corr", C.c_int),
     ]
 
 
@@ -136,6 +136,7 @@ def make_params(d: dict) -> OrcParams:
         setattr(p, k, float(d[k]))
     for k in ("l_base", "l_max", "isothermal", "coll_ion"):
         setattr(p, k, int(d[k]))
+    p.geo_corr = int(d.get("geo_corr", 0))
     return p
 
 

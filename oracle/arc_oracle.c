@@ -252,6 +252,42 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
         double ns[3];
         absorbers(c, idx, ns);
         const double L = ds * c->dx;
+
+        /* Sec. 2.5, Eq. (correction): the ray stands for a cone of width
+         * L_pix = r sqrt(Omega_l) at the segment's midpoint; when that point is
+         * closer than L_pix / 2 to the nearest face of the cell, only the
+         * fraction f_c = 1/2 + D_edge / L_pix of the absorption stays in the
+         * cell and 1 - f_c goes to the neighbour across that face
+         * (Eq. correction2, read as photons: the neighbour takes them with its
+         * own absorber shares, so the photon count is unchanged). */
+        double fc = 1.0;
+        int64_t nidx = -1;
+        double nkap[ORC_MAXG] = {0};
+        if (p->geo_corr && ds > 0.0) {
+            const double rm = 0.5 * (r + r1);
+            double dmin = INFINITY;
+            int nax = 0, nside = 0;
+            for (int a = 0; a < 3; a++) {
+                const double f = o[a] + rm * u[a] - (double)cell[a];   /* position inside the cell */
+                if (f < dmin) { dmin = f; nax = a; nside = -1; }
+                if (1.0 - f < dmin) { dmin = 1.0 - f; nax = a; nside = 1; }
+            }
+            if (dmin < 0.0) dmin = 0.0;
+            const double lpix = rm * sqrt(4.0 * PI / (12.0 * pow(4.0, level)));   /* width: sqrt of Omega_l */
+            int nb[3] = {cell[0], cell[1], cell[2]};
+            nb[nax] += nside;
+            if (dmin < 0.5 * lpix && nb[nax] >= 0 && nb[nax] < n) {
+                fc = 0.5 + dmin / lpix;
+                nidx = ((int64_t)nb[0] * n + nb[1]) * n + nb[2];
+                double nns[3];
+                absorbers(c, nidx, nns);
+                for (int b = 0; b < G; b++) {
+                    double kb = 0.0;
+                    for (int s = 0; s < 3; s++) kb += p->sigma[s][b] * nns[s];
+                    nkap[b] = kb * c->dx;
+                }
+            }
+        }
         for (int b = 0; b < G; b++) {
             double kb = 0.0;
             for (int s = 0; s < 3; s++) kb += p->sigma[s][b] * ns[s];
@@ -261,7 +297,13 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
                 const double A = N[b] * (-expm1(-dtau));
                 N[b] -= A;
                 c->absorbed += A;
-                deposit(c, idx, b, A, kap[b]);
+                if (nidx >= 0 && nkap[b] > 0.0) {
+                    /* a neighbour without absorbers of this group takes nothing */
+                    deposit(c, idx, b, fc * A, kap[b]);
+                    deposit(c, nidx, b, (1.0 - fc) * A, nkap[b]);
+                } else {
+                    deposit(c, idx, b, A, kap[b]);
+                }
             }
         }
         visits++;

@@ -43,6 +43,8 @@ typedef struct {
     double alpha_B_fixed;          /* > 0: constant HII case-B coefficient          */
     int    coll_ion;               /* 1: collisional ionisation on                  */
     double z_compton;              /* >= 0: Compton cooling off the CMB at this z   */
+    int    geo_corr;               /* 1: geometric correction f_c with the secondary
+                                      f'_c to the nearest neighbour (Sec. 2.5)      */
 } orc_params;
 
 /* end reasons of a ray */
