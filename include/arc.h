@@ -85,6 +85,13 @@ typedef struct {
     double alpha_B_fixed;                 /* > 0: constant case-B alpha_HII [cm^3/s]   */
     int coll_ion;                         /* 1: collisional ionisation on              */
     double z_compton;                     /* >= 0: Compton cooling off the CMB at z    */
+    int geo_correction;                   /* 1: geometric correction (Sec. 2.5, Eqs.
+                                             correction, correction2): when a segment's
+                                             midpoint is within half a pixel width
+                                             L = r sqrt(Omega_l) of the nearest cell
+                                             face, 1 - f_c (f_c = 1/2 + D_edge / L) of
+                                             its absorbed photons go to the neighbour
+                                             across that face; 0: off                  */
 } arc_params;
 
 /* Counters of the last arc_trace / arc_chem_update (arc_stats synchronises). */

@@ -109,6 +109,8 @@ def lib(path: Optional[str] = None):
         L.orc_trace.argtypes = [C.POINTER(OrcParams), dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp,
                                 C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.orc_trace.restype = C.c_int
+        L.orc_trace_ex.argtypes = L.orc_trace.argtypes + [C.c_void_p]
+        L.orc_trace_ex.restype = C.c_int
         L.orc_chem.argtypes = [C.POINTER(OrcParams), C.c_int64, dp, dp, dp, dp, dp, dp, dp,
                                C.c_double, C.POINTER(C.c_int64)]
         L.orc_chem.restype = C.c_int
@@ -162,7 +164,7 @@ def r_split(params: dict, level: int) -> float:
 
 
 def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool = False,
-          rec_cap: int = 1 << 22):
+          rec_cap: int = 1 << 22, corr_margin: bool = False):
     """One RT pass.  Returns dict(gamma[3,n,n,n], heat[3,n,n,n], budget[3],
     nseg, nrec, recs (structured array or None))."""
     p = make_params(params)
@@ -178,17 +180,19 @@ def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool =
     nrec = C.c_int64(0)
     nseg = C.c_int64(0)
     recs = np.zeros(rec_cap if records else 0, dtype=REC_DTYPE)
-    rc = lib().orc_trace(C.byref(p), _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII), nsrc,
-                         _dptr(pos), _dptr(ndot), _dptr(gamma), _dptr(heat), _dptr(budget),
-                         recs.ctypes.data if records else None, rec_cap if records else 0,
-                         C.byref(nrec), C.byref(nseg))
+    cm = np.zeros(n ** 3 if corr_margin else 0)
+    rc = lib().orc_trace_ex(C.byref(p), _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII), nsrc,
+                            _dptr(pos), _dptr(ndot), _dptr(gamma), _dptr(heat), _dptr(budget),
+                            recs.ctypes.data if records else None, rec_cap if records else 0,
+                            C.byref(nrec), C.byref(nseg), cm.ctypes.data if corr_margin else None)
     if rc == -2:
         raise RuntimeError(f"oracle record buffer too small: {nrec.value} > {rec_cap}")
     if rc != 0:
         raise ValueError(f"orc_trace failed ({rc})")
     return dict(gamma=gamma.reshape(3, n, n, n), heat=heat.reshape(3, n, n, n), budget=budget,
                 nseg=int(nseg.value), nrec=int(nrec.value),
-                recs=recs[: nrec.value] if records else None)
+                recs=recs[: nrec.value] if records else None,
+                corr_margin=cm.reshape(n, n, n) if corr_margin else None)
 
 
 def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float, min_sub: int = 0):

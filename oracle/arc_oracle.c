@@ -167,6 +167,8 @@ typedef struct {
     const double* o;      /* current source position */
     uint32_t isrc;
     double thr_base;      /* term_frac * photons of one ray at l_base */
+    double* cmargin;      /* optional: per cell, smallest face-tie margin of the
+                             geometric corrections that touched it [cells] */
 } tctx;
 
 /* absorber densities n_HI, n_HeI, n_HeII of a cell [cm^-3] (Sec. 2.3) */
@@ -265,15 +267,37 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
         double nkap[ORC_MAXG] = {0};
         if (p->geo_corr && ds > 0.0) {
             const double rm = 0.5 * (r + r1);
-            double dmin = INFINITY;
-            int nax = 0, nside = 0;
+            double dmin = INFINITY, d2 = INFINITY;
+            int nax = 0, nside = 0, aax = 0, aside = 0;
             for (int a = 0; a < 3; a++) {
                 const double f = o[a] + rm * u[a] - (double)cell[a];   /* position inside the cell */
-                if (f < dmin) { dmin = f; nax = a; nside = -1; }
-                if (1.0 - f < dmin) { dmin = 1.0 - f; nax = a; nside = 1; }
+                const double dd[2] = {f, 1.0 - f};
+                for (int k = 0; k < 2; k++) {
+                    if (dd[k] < dmin) {
+                        d2 = dmin; aax = nax; aside = nside;
+                        dmin = dd[k]; nax = a; nside = k ? 1 : -1;
+                    } else if (dd[k] < d2) {
+                        d2 = dd[k]; aax = a; aside = k ? 1 : -1;
+                    }
+                }
             }
             if (dmin < 0.0) dmin = 0.0;
             const double lpix = rm * sqrt(4.0 * PI / (12.0 * pow(4.0, level)));   /* width: sqrt of Omega_l */
+            if (c->cmargin && dmin < 0.5 * lpix) {
+                /* which face is nearest is a discontinuous decision: note how
+                 * close it was in the cells whose deposit depends on it */
+                const double mg = d2 - dmin;
+                int alt[3] = {cell[0], cell[1], cell[2]}, nn[3] = {cell[0], cell[1], cell[2]};
+                alt[aax] += aside;
+                nn[nax] += nside;
+                c->cmargin[idx] = fmin(c->cmargin[idx], mg);
+                if (nn[nax] >= 0 && nn[nax] < n)
+                    c->cmargin[((int64_t)nn[0] * n + nn[1]) * n + nn[2]] =
+                        fmin(c->cmargin[((int64_t)nn[0] * n + nn[1]) * n + nn[2]], mg);
+                if (alt[aax] >= 0 && alt[aax] < n)
+                    c->cmargin[((int64_t)alt[0] * n + alt[1]) * n + alt[2]] =
+                        fmin(c->cmargin[((int64_t)alt[0] * n + alt[1]) * n + alt[2]], mg);
+            }
             int nb[3] = {cell[0], cell[1], cell[2]};
             nb[nax] += nside;
             if (dmin < 0.5 * lpix && nb[nax] >= 0 && nb[nax] < n) {
@@ -378,12 +402,24 @@ int orc_trace(const orc_params* p, const double* nH, const double* xHI,
               int nsrc, const double* pos, const double* ndot,
               double* gamma, double* heat, double* budget,
               orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg) {
+    return orc_trace_ex(p, nH, xHI, xHeI, xHeII, nsrc, pos, ndot, gamma, heat, budget, recs, rec_cap, nrec,
+                        nseg, NULL);
+}
+
+int orc_trace_ex(const orc_params* p, const double* nH, const double* xHI,
+                 const double* xHeI, const double* xHeII,
+                 int nsrc, const double* pos, const double* ndot,
+                 double* gamma, double* heat, double* budget,
+                 orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg, double* corr_margin) {
     if (!p || p->n <= 0 || p->ngroups < 1 || p->ngroups > ORC_MAXG || p->l_base < 1 ||
         p->l_max < p->l_base || p->phi <= 0.0 || nsrc < 0)
         return -1;
     tctx c;
     memset(&c, 0, sizeof c);
     c.p = p;
+    c.cmargin = corr_margin;
+    if (corr_margin)
+        for (int64_t i = 0; i < (int64_t)p->n * p->n * p->n; i++) corr_margin[i] = INFINITY;
     c.nH = nH;
     c.xHI = xHI;
     c.xHeI = xHeI;

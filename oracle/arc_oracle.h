@@ -89,6 +89,14 @@ int orc_trace(const orc_params* p, const double* nH, const double* xHI,
               int nsrc, const double* pos, const double* ndot,
               double* gamma, double* heat, double* budget,
               orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg);
+/* The same, and with corr_margin (n^3, may be NULL) also, per cell, the
+ * smallest margin (second-nearest minus nearest face distance [cells]) of
+ * the geometric-correction face choices whose deposits touched the cell. */
+int orc_trace_ex(const orc_params* p, const double* nH, const double* xHI,
+                 const double* xHeI, const double* xHeII,
+                 int nsrc, const double* pos, const double* ndot,
+                 double* gamma, double* heat, double* budget,
+                 orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg, double* corr_margin);
 
 /*
  * Sub-cycled chemistry / energy update of ncell cells over dt seconds

@@ -46,6 +46,7 @@ class ArcParams(C.Structure):
         ("l_base", C.c_int), ("l_max", C.c_int), ("term_frac", C.c_double),
         ("eps_sub", C.c_double), ("x_fp64", C.c_double), ("isothermal", C.c_int),
         ("alpha_B_fixed", C.c_double), ("coll_ion", C.c_int), ("z_compton", C.c_double),
+        ("geo_correction", C.c_int),
     ]
 
 
@@ -147,6 +148,7 @@ def make_params(d: dict) -> ArcParams:
         setattr(p, k, float(d[k]))
     for k in ("l_base", "l_max", "isothermal", "coll_ion"):
         setattr(p, k, int(d[k]))
+    p.geo_correction = int(d.get("geo_corr", 0))
     return p
 
 

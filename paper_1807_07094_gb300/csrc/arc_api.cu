@@ -141,6 +141,8 @@ arc_status check_params(arc_ctx* c, const arc_grid* g, const arc_params* p) {
     if (!(p->Y >= 0 && p->Y < 1)) return fail(c, ARC_E_INVALID, "Y outside [0,1)");
     if (!(p->phi > 0) || !isfinite(p->phi)) return fail(c, ARC_E_INVALID, "phi must be > 0");
     if (p->l_base < 1 || p->l_base > 6) return fail(c, ARC_E_INVALID, "l_base outside 1..6");
+    if (p->geo_correction != 0 && p->geo_correction != 1)
+        return fail(c, ARC_E_INVALID, "geo_correction must be 0 or 1");
     if (p->l_max < p->l_base || p->l_max > ARC_MAX_LEVEL)
         return fail(c, ARC_E_INVALID, "l_max outside l_base..%d", ARC_MAX_LEVEL);
     if (!(p->term_frac > 0 && p->term_frac < 1)) return fail(c, ARC_E_INVALID, "term_frac outside (0,1)");
@@ -256,7 +258,11 @@ TraceArgs trace_args(arc_ctx* c) {
     a.acc = c->rec;
     a.src = c->dsrc;
     a.nsrc = c->nsrc_dev;
-    for (int l = 0; l <= ARC_MAX_LEVEL; ++l) a.rsplit[l] = c->rsplit[l];
+    for (int l = 0; l <= ARC_MAX_LEVEL; ++l) {
+        a.rsplit[l] = c->rsplit[l];
+        a.pixw[l] = (float)sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * l)));   // Omega_l = 4 pi / (12 4^l)
+    }
+    a.geo_corr = c->p.geo_correction ? 1 : 0;
     a.seeds = c->seeds;
     a.nseeds = c->nseeds;
     a.seed_head = &c->scal->seed_head;

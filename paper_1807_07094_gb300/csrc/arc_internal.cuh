@@ -90,6 +90,8 @@ struct TraceArgs {
     const SourceDev* src;
     int nsrc;
     float rsplit[ARC_MAX_LEVEL + 1];   // split distance per level [cells]
+    float pixw[ARC_MAX_LEVEL + 1];     // pixel width per unit distance, sqrt(Omega_l)
+    int geo_corr;                      // geometric correction (Sec. 2.5) on
     // emitted work: static array consumed by ticket
     const Entry* seeds;
     int nseeds;

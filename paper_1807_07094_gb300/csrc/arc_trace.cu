@@ -389,6 +389,7 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
     if (NG > 2) sumN += R.N.z;
     if (NG > 3) sumN += R.N.w;
     const bool term = sumN < R.thr;
+    const float4 Dabs = D;   // this segment's Eq. (ion) absorption
     if (term) {
         // below threshold: every remaining photon stays in this cell
         D = make_float4(Nh0.x, NG > 1 ? Nh0.y : 0.f, NG > 2 ? Nh0.z : 0.f, NG > 3 ? Nh0.w : 0.f);
@@ -397,6 +398,44 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
         R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (REC) R.visits++;   // per-ray records only
+    // Sec. 2.5, Eq. (correction): near a face of the cell (midpoint closer than
+    // half the pixel width) the fraction 1 - f_c of the photons absorbed here
+    // goes to the neighbour across that face (Eq. correction2, as photons split
+    // over the neighbour's own absorbers in k_finalize).  The moved part is
+    // taken from the absorbed part only; at a termination the residual stays.
+    uint64_t nidx = 0;
+    float4 Dn = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool corr = false;
+    if (A.geo_corr && ds > 0.0f) {
+        const float rm = 0.5f * (R.r + r1);
+        const float ux = __frcp_rn(R.ix), uy = __frcp_rn(R.iy), uz = __frcp_rn(R.iz);   // 1/inf = 0
+        const float f[3] = {fmaf(rm, ux, R.ox) - (float)R.cx, fmaf(rm, uy, R.oy) - (float)R.cy,
+                            fmaf(rm, uz, R.oz) - (float)R.cz};
+        float dmin = INFINITY;
+        int nax = 0, nside = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {   // faces -x, +x, -y, +y, -z, +z; ties to the first
+            if (f[a] < dmin) { dmin = f[a]; nax = a; nside = -1; }
+            if (1.0f - f[a] < dmin) { dmin = 1.0f - f[a]; nax = a; nside = 1; }
+        }
+        dmin = fmaxf(dmin, 0.0f);
+        const float lpix = rm * A.pixw[R.level];
+        int nb[3] = {R.cx, R.cy, R.cz};
+        nb[nax] += nside;
+        if (dmin < 0.5f * lpix && nb[nax] >= 0 && nb[nax] < A.n) {
+            const float fc = 0.5f + __fdividef(dmin, lpix);
+            nidx = brick_index(nb[0], nb[1], nb[2], A.nb);
+            const float4 nk = ldg_f4(&A.kappa[2 * nidx]);
+            // moved photons per group (none where the neighbour has no absorber);
+            // d - moved is exact because moved <= d / 2
+            const float g = 1.0f - fc;
+            Dn.x = nk.x > 0.f ? __fmul_rn(g, Dabs.x) : 0.f;
+            if (NG > 1) Dn.y = nk.y > 0.f ? __fmul_rn(g, Dabs.y) : 0.f;
+            if (NG > 2) Dn.z = nk.z > 0.f ? __fmul_rn(g, Dabs.z) : 0.f;
+            if (NG > 3) Dn.w = nk.w > 0.f ? __fmul_rn(g, Dabs.w) : 0.f;
+            corr = Dn.x != 0.f || Dn.y != 0.f || Dn.z != 0.f || Dn.w != 0.f;
+        }
+    }
     R.r = r1;
     int ev = term ? EV_TERM : (split ? EV_SPLIT : EV_NONE);
     if (ev == EV_NONE) {
@@ -422,6 +461,13 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
             R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
             R.kap = ldg_f4(&A.kappa[2 * R.idx]);
         }
+    }
+    if (corr) {
+        D.x = __fsub_rn(D.x, Dn.x);   // exact: Dn <= D / 2
+        D.y = __fsub_rn(D.y, Dn.y);
+        D.z = __fsub_rn(D.z, Dn.z);
+        D.w = __fsub_rn(D.w, Dn.w);
+        rerr = __fadd_rn(rerr, deposit<NG>(A.acc, nidx, Dn, make_float4(0.f, 0.f, 0.f, 0.f)));
     }
     if (D.x != 0.f || D.y != 0.f || D.z != 0.f || D.w != 0.f || E.x != 0.f || E.y != 0.f ||
         E.z != 0.f || E.w != 0.f)
