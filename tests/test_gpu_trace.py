@@ -206,8 +206,9 @@ def test_geometric_correction_matches_oracle(seed):
     paper's 'nearest adjacent cell' is then undefined), which FP32 and FP64
     break differently; cells whose deposits depend on a choice closer than 4
     FP32 ulps of the largest distance (2n cells) are left out.  f_c itself
-    depends on the FP32 midpoint (ulp up to 7.6e-6 cells against pixel widths
-    of ~0.25 cells), so the rates carry up to ~3e-4 relative error."""
+    depends on D_edge / L_pix, D_edge from the FP32 midpoint (error up to ~4
+    ulps of 2n cells, 3e-5) and L_pix down to ~0.05 cells next to a source, so
+    the rates carry up to ~6e-4 relative error there: the bar is 1e-3."""
     w = W.cosmic(n=48, nsrc=6, sigma_ln=1.5, seed=seed)
     xs = partly_ionised(w, seed=seed + 10, lo=-4, hi=0)
     p = dict(w.params(), geo_corr=1)
@@ -230,7 +231,7 @@ def test_geometric_correction_matches_oracle(seed):
             ref = o[name][s]
             m = keep & (ref > 1e-6 * ref.max())
             rel = np.abs(g[name][s][m] - ref[m]) / ref[m]
-            assert rel.max() <= 3e-4, (name, s, float(rel.max()), int(m.sum()))
+            assert rel.max() <= 1e-3, (name, s, float(rel.max()), int(m.sum()))
 
 
 def test_autotune_picks_a_shape_and_keeps_results():
