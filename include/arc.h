@@ -270,6 +270,18 @@ arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, const float
  */
 arc_status arc_autotune(arc_ctx* ctx, int max_sources, int reps, double* best_ms);
 
+/*
+ * arc_rt_timestep -- radiative-transfer time step (Sec. 2.9) from the
+ * context's current fields and the HI photoionisation rate of the last
+ * arc_trace.  Per cell dn_HI/dt = alpha n_e n_HII - (Gamma_HI + beta n_e) n_HI
+ * (Eq. anninos); *dt_n = min over cells with n_HI sigma d > 0.5 of
+ * eps n_HI / |dn_HI/dt| ("minimum neutral fraction change"), *dt_I = min over
+ * all cells of eps / (sigma d |dn_HI/dt|) ("minimum intensity change"); sigma
+ * is the HI cross section of the first group, d the cell width; seconds,
+ * +inf when no cell qualifies.  FP32 per cell.  Synchronises.
+ */
+arc_status arc_rt_timestep(arc_ctx* ctx, double eps, double* dt_n, double* dt_I);
+
 /* ------------------------------------------------------------------------
  * Chemistry surrogate (a learned stand-in for the sub-cycled update of
  * arc_chem_update; the paper has none).  Per cell a physics predictor -- the

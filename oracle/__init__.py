@@ -118,6 +118,8 @@ def lib(path: Optional[str] = None):
                                        C.c_double, C.c_int, C.POINTER(C.c_int64)]
         L.orc_chem_refined.restype = C.c_int
         L.orc_rates.argtypes = [C.POINTER(OrcParams), C.c_double, dp]
+        L.orc_rt_timestep.argtypes = [C.POINTER(OrcParams), C.c_int64, dp, dp, dp, dp, dp, dp, C.c_double, dp]
+        L.orc_rt_timestep.restype = None
         L.orc_cooling.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double, C.c_double]
         L.orc_cooling.restype = C.c_double
@@ -214,6 +216,17 @@ def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float, min_sub:
         capped = lib().orc_chem(C.byref(p), ncell, _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII),
                                 _dptr(T), _dptr(g), _dptr(h), float(dt), C.byref(nsub))
     return xHI, xHeI, xHeII, T, int(nsub.value), int(capped)
+
+
+def rt_timestep(params: dict, nH, xHI, xHeI, xHeII, T, gamma_HI, eps: float):
+    """Sec. 2.9: (min dt_n over cells with n_HI sigma d > 0.5, min dt_I) [s]."""
+    p = make_params(params)
+    f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    nH, xHI, xHeI, xHeII, T, g = f(nH), f(xHI), f(xHeI), f(xHeII), f(T), f(gamma_HI)
+    out = np.zeros(2)
+    lib().orc_rt_timestep(C.byref(p), nH.size, _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII), _dptr(T),
+                          _dptr(g), float(eps), _dptr(out))
+    return float(out[0]), float(out[1])
 
 
 def rates(params: dict, T: float) -> np.ndarray:

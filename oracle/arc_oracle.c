@@ -632,3 +632,37 @@ int orc_chem_refined(const orc_params* p, int64_t ncell, const double* nHa,
     if (min_sub < 1) return -1;
     return chem_subcycled(p, ncell, nHa, xHI, xHeI, xHeII, Ta, gamma, heat, dt, min_sub, nsub_out);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Radiative-transfer time step (Sec. 2.9), from the current state and the   */
+/* rates of the last trace.  Per cell, with dn_HI/dt = alpha n_e n_HII -      */
+/* (Gamma_HI + beta n_e) n_HI (Eq. anninos):                                  */
+/*   dt_n = eps n_HI / |dn_HI/dt| over the cells with tau = n_HI sigma d > 0.5  */
+/*   dt_I = eps / (sigma d |dn_HI/dt|)  over all cells                          */
+/* with sigma the HI cross section of the lowest group and d the cell width;  */
+/* out[0] = min dt_n, out[1] = min dt_I (+inf when no cell qualifies).        */
+/* ------------------------------------------------------------------------- */
+void orc_rt_timestep(const orc_params* p, int64_t ncell, const double* nHa, const double* xHI,
+                     const double* xHeI, const double* xHeII, const double* Ta, const double* gamma,
+                     double eps, double out[2]) {
+    const double y = p->Y / (4.0 * (1.0 - p->Y));
+    const double d = p->box_cm / p->n;
+    const double sig = p->sigma[0][0];
+    double dtn = INFINITY, dti = INFINITY;
+    for (int64_t i = 0; i < ncell; i++) {
+        const double nH = nHa[i];
+        if (!(nH > 0.0)) continue;
+        const double nHe = y * nH;
+        const double nHI = xHI[i] * nH, nHeI = xHeI[i] * nHe, nHeII = xHeII[i] * nHe;
+        const double ne = (nH - nHI) + nHeII + 2.0 * (nHe - nHeI - nHeII);
+        double r[6];
+        orc_rates(p, Ta[i], r);
+        const double rate = fabs(r[0] * ne * (nH - nHI) - (gamma[i] + r[3] * ne) * nHI);
+        if (!(rate > 0.0)) continue;
+        if (nHI * sig * d > 0.5) dtn = fmin(dtn, eps * nHI / rate);
+        dti = fmin(dti, eps / (sig * d * rate));
+    }
+    out[0] = dtn;
+    out[1] = dti;
+}
+

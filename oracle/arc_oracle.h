@@ -119,6 +119,14 @@ int orc_chem_refined(const orc_params* p, int64_t ncell, const double* nH,
                      const double* gamma, const double* heat, double dt, int min_sub,
                      int64_t* nsub);
 
+/* Radiative-transfer time step (Sec. 2.9) from the current state and the HI
+ * photoionisation rate of the last trace (gamma: ncell values):
+ * out[0] = min over cells with n_HI sigma d > 0.5 of eps n_HI / |dn_HI/dt|,
+ * out[1] = min over cells of eps / (sigma d |dn_HI/dt|); +inf if none. */
+void orc_rt_timestep(const orc_params* p, int64_t ncell, const double* nH, const double* xHI,
+                     const double* xHeI, const double* xHeII, const double* T, const double* gamma,
+                     double eps, double out[2]);
+
 /* Rate coefficients at temperature T (for tests):
  * out[0..5] = alpha_HII, alpha_HeII(+dielectronic), alpha_HeIII,
  *             beta_HI, beta_HeI, beta_HeII  [cm^3/s]. */

@@ -102,6 +102,7 @@ _SIGS = {
     "arc_mlp_trainer_destroy": ([C.c_void_p], None),
     "arc_mlp_eval": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
     "arc_mlp_features": ([C.c_void_p] * 7 + [C.c_double, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
+    "arc_rt_timestep": ([C.c_void_p, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "arc_mlp_targets": ([C.c_void_p] * 8 + [C.c_double, C.c_longlong, C.c_void_p], C.c_int),
 }
 
@@ -502,6 +503,12 @@ class Arc:
 
     def set_surrogate(self, params=None, norm=None, tol_x: float = 5e-4, tol_e: float = 1e-2, gate: float = 0.0):
         arc_set_surrogate(self.ctx, params, norm, tol_x, tol_e, gate)
+
+    def rt_timestep(self, eps: float = 0.1):
+        """(dt_n, dt_I) [s] of Sec. 2.9 from the current state and the last trace."""
+        a, b = C.c_double(), C.c_double()
+        _check(self.ctx, load().arc_rt_timestep(C.c_void_p(self.ctx), float(eps), C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def mlp_targets(self, nH, x0, T0, gamma, heat, x1, T1, dt: float, Y):
         arc_mlp_targets(self.ctx, nH, x0, T0, gamma, heat, x1, T1, dt, Y)

@@ -720,6 +720,36 @@ arc_status arc_set_surrogate(arc_ctx* c, const float* params, const float* norm,
     return ARC_OK;
 }
 
+arc_status arc_rt_timestep(arc_ctx* c, double eps, double* dt_n, double* dt_I) {
+    if (!c) return ARC_E_INVALID;
+    if (!c->fields_set) return fail(c, ARC_E_STATE, "arc_set_fields must come first");
+    if (!(eps > 0) || !isfinite(eps) || !dt_n || !dt_I) return fail(c, ARC_E_INVALID, "eps <= 0 or null output");
+    ChemArgs C = chem_args(c, 0.0);
+    C.ncell = (long long)c->n * c->n * c->n;
+    C.nH = c->nH;
+    C.xHI = c->xHI;
+    C.xHeI = c->xHeI;
+    C.xHeII = c->xHeII;
+    C.T = c->T;
+    C.gamma = c->gamma;   // Gamma_HI of the last trace (zero before any trace)
+    unsigned* out = nullptr;
+    CK(dalloc(&out, 2));
+    const unsigned inf_bits[2] = {0x7f800000u, 0x7f800000u};
+    cudaError_t e = cudaMemcpyAsync(out, inf_bits, sizeof inf_bits, cudaMemcpyHostToDevice, c->stream);
+    const float sigd = (float)(c->p.sigma[0][0] * c->dx);
+    if (e == cudaSuccess) e = launch_rt_timestep(C, sigd, (float)eps, out, c->stream);
+    unsigned bits[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits, out, sizeof bits, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(out);
+    if (e != cudaSuccess) return fail(c, ARC_E_CUDA, "arc_rt_timestep: %s", cudaGetErrorString(e));
+    float f[2];
+    memcpy(f, bits, sizeof f);
+    *dt_n = (double)f[0];
+    *dt_I = (double)f[1];
+    return ARC_OK;
+}
+
 arc_status arc_mlp_targets(arc_ctx* c, const float* nH, const float* x0, const float* T0, const float* gamma,
                            const float* heat, const float* x1, const float* T1, double dt, long long n, float* Y) {
     if (!c) return ARC_E_INVALID;

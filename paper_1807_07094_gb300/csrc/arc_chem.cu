@@ -695,6 +695,46 @@ cudaError_t launch_mlp_targets(const ChemArgs& c, const float* x1, const float* 
     return cudaGetLastError();
 }
 
+// Radiative-transfer time step (Sec. 2.9): per cell dn_HI/dt from the current
+// state and the last trace's Gamma_HI (Eq. anninos); out[0] = min of
+// eps n_HI / |dn_HI/dt| over cells with n_HI sigma d > 0.5, out[1] = min of
+// eps / (sigma d |dn_HI/dt|) over all cells.  Positive floats order like their
+// bit patterns, so the minima are integer atomics on them (out preset to +inf).
+__global__ void k_rt_timestep(const ChemArgs C, float sigd, float eps, unsigned* out) {
+    float dtn = INFINITY, dti = INFINITY;
+    const float y = C.y;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float nH = C.nH[c];
+        if (!(nH > 0.0f)) continue;
+        const float a0 = C.xHI[c], a1 = y * C.xHeI[c], a2 = y * C.xHeII[c];
+        const float xe = (1.0f - a0) + a2 + 2.0f * (y - a1 - a2);
+        const Coef r = coefficients(C.T[c], C);
+        const float ne = nH * xe;
+        const float nHI = a0 * nH;
+        const float rate = fabsf(r.aH * ne * (nH - nHI) - (C.gamma[c] + r.b0 * ne) * nHI);
+        if (!(rate > 0.0f)) continue;
+        if (nHI * sigd > 0.5f) dtn = fminf(dtn, eps * nHI / rate);
+        dti = fminf(dti, eps / (sigd * rate));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dtn = fminf(dtn, __shfl_down_sync(0xFFFFFFFFu, dtn, o));
+        dti = fminf(dti, __shfl_down_sync(0xFFFFFFFFu, dti, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&out[0], __float_as_uint(dtn));
+        atomicMin(&out[1], __float_as_uint(dti));
+    }
+}
+
+cudaError_t launch_rt_timestep(const ChemArgs& c, float sigd, float eps, unsigned* out, cudaStream_t s) {
+    long long blocks = (c.ncell + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_rt_timestep<<<(int)blocks, 256, 0, s>>>(c, sigd, eps, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chem(const ChemArgs& a, cudaStream_t s) {
     long long blocks = (a.ncell + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;

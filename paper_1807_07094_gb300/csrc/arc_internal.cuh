@@ -253,6 +253,7 @@ cudaError_t launch_validate(const float* nH, const float* xHI, const float* xHeI
 cudaError_t launch_make_seeds(const SourceDev* src, int nsrc, int l_base, Entry* seeds,
                               cudaStream_t s);
 cudaError_t launch_chem(const ChemArgs& a, cudaStream_t s);
+cudaError_t launch_rt_timestep(const ChemArgs& c, float sigd, float eps, unsigned* out, cudaStream_t s);
 int trace_smem_bytes(int block, int stack_log2);
 const void* trace_kernel_ptr(int ng, bool rec = false);   // rec: the per-ray-record variant
 

@@ -113,3 +113,26 @@ def test_graph_step_matches_eager():
     b = free_run_gpu(w, 3, True)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-6 * max(1.0, np.abs(x).max())
+
+
+def test_rt_timestep_matches_oracle():
+    """Sec. 2.9 time-step minima on random gas and rates: the GPU reduction
+    against the oracle's loop over the same cells."""
+    n = 16
+    m = n ** 3
+    nH, xHI, xHeI, xHeII, T = W.random_gas(m, 7)
+    gamma, heat = W.random_rates(m, 7, gmax=1e-12)
+    p = dict(W.thermal_128().params(), n=n, box_cm=1e21 * n)
+    sh = (n, n, n)
+    with P.Arc(n, 1e21 * n, p) as a:
+        a.set_fields(nH.reshape(sh), xHI.reshape(sh), xHeI.reshape(sh), xHeII.reshape(sh), T.reshape(sh))
+        g, h, _ = a.trace(1.0, budget=False)        # no sources: allocates and zeroes the rates
+        torch.cuda.synchronize()
+        g.copy_(torch.from_numpy(gamma.reshape(3, n, n, n)).cuda())
+        torch.cuda.synchronize()
+        dtn, dti = a.rt_timestep(0.1)
+    f64 = lambda v: np.asarray(v, np.float64)
+    odtn, odti = oracle.rt_timestep(p, f64(nH), f64(xHI), f64(xHeI), f64(xHeII), f64(T), f64(gamma[0]), 0.1)
+    assert np.isfinite(odtn) and np.isfinite(odti)
+    assert abs(dtn / odtn - 1) < 1e-5, (dtn, odtn)
+    assert abs(dti / odti - 1) < 1e-5, (dti, odti)

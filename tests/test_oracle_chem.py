@@ -226,3 +226,28 @@ def test_refined_update_converges_to_riccati_solution():
         assert abs(2 * errs[400] - errs[200]) < 0.03 * abs(errs[200]), errs   # first order in 1/m
         x, *_ = run_cell(p, nH, 1 - u0, 0.0, 0.0, 1e4, [G, 0, 0], [0, 0, 0], t)
         assert abs(errs[400]) < abs(x[0] - exact) < 0.02
+
+
+def test_rt_timestep_single_cell_closed_form():
+    """Sec. 2.9 for one cell, pure H, fixed alpha, no collisions: dn_HI/dt =
+    alpha n_e n_HII - Gamma n_HI with n_e = n_HII, so dt_n and dt_I follow by
+    hand; a cell with tau = n_HI sigma d <= 0.5 is left out of dt_n."""
+    alpha, G, eps = 2.59e-13, 1e-12, 0.1
+    p = params(alpha_B_fixed=alpha)
+    d = p["box_cm"] / p["n"]
+    sig = p["sigma"][0][0]
+    for nH, x in ((1e-2, 0.9), (1e-2, 0.3), (1e-5, 0.5)):
+        nHI, nHII = x * nH, (1 - x) * nH
+        rate = abs(alpha * nHII * nHII - G * nHI)
+        dtn, dti = oracle.rt_timestep(p, [nH], [x], [0.0], [0.0], [1e4], [G], eps)
+        assert abs(dti / (eps / (sig * d * rate)) - 1) < 1e-12
+        if nHI * sig * d > 0.5:
+            assert abs(dtn / (eps * nHI / rate) - 1) < 1e-12
+        else:
+            assert dtn == math.inf
+    # the minimum over cells is the smallest single-cell value
+    nH = np.array([1e-2, 1e-2, 2e-2])
+    x = np.array([0.9, 0.5, 0.95])
+    one = [oracle.rt_timestep(p, [a], [b], [0.0], [0.0], [1e4], [G], eps) for a, b in zip(nH, x)]
+    both = oracle.rt_timestep(p, nH, x, np.zeros(3), np.zeros(3), np.full(3, 1e4), np.full(3, G), eps)
+    assert both == (min(o[0] for o in one), min(o[1] for o in one))
