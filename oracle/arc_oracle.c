@@ -653,11 +653,12 @@ void orc_rt_timestep(const orc_params* p, int64_t ncell, const double* nHa, cons
         const double nH = nHa[i];
         if (!(nH > 0.0)) continue;
         const double nHe = y * nH;
-        const double nHI = xHI[i] * nH, nHeI = xHeI[i] * nHe, nHeII = xHeII[i] * nHe;
-        const double ne = (nH - nHI) + nHeII + 2.0 * (nHe - nHeI - nHeII);
+        const double nHI = xHI[i] * nH, nHeII = xHeII[i] * nHe;
+        const double nHeIII = nHe - xHeI[i] * nHe - nHeII;
+        const double n_e = (nH - nHI) + nHeII + 2.0 * nHeIII;   /* Sec. 2.3 */
         double r[6];
         orc_rates(p, Ta[i], r);
-        const double rate = fabs(r[0] * ne * (nH - nHI) - (gamma[i] + r[3] * ne) * nHI);
+        const double rate = fabs(r[0] * n_e * (nH - nHI) - (gamma[i] + r[3] * n_e) * nHI);
         if (!(rate > 0.0)) continue;
         if (nHI * sig * d > 0.5) dtn = fmin(dtn, eps * nHI / rate);
         dti = fmin(dti, eps / (sig * d * rate));
