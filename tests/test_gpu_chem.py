@@ -112,7 +112,10 @@ def test_graph_step_matches_eager():
     a = free_run_gpu(w, 3, False)
     b = free_run_gpu(w, 3, True)
     for x, y in zip(a, b):
-        assert np.abs(x - y).max() <= 1e-6 * max(1.0, np.abs(x).max())
+        # the cell sums are FP32 atomics, so two runs differ by the order of
+        # the additions (~1e-7 relative per cell), which three chemistry
+        # steps carry to a few 1e-6
+        assert np.abs(x - y).max() <= 1e-5 * max(1.0, np.abs(x).max())
 
 
 def test_rt_timestep_matches_oracle():
