@@ -106,7 +106,7 @@ __device__ __forceinline__ float two_sum_err(float a, float b) {
 __device__ __forceinline__ float absorbed_fraction(float tau) {
     // 1 - e^-tau: degree-6 Taylor polynomial below tau = 1/8 (relative
     // truncation error < tau^6/5040 < 8e-10), the hardware exponential above
-    // (absolute error ~2e-7 e^-tau, relative < 2e-6 there).  Photon
+    // (used only while a < 1/2, i.e. tau < ln 2: relative error < 2e-6).  Photon
     // conservation does not depend on it: the ray loses exactly what the cell
     // receives.
     if (tau < 0.125f) {
@@ -128,7 +128,10 @@ __device__ __forceinline__ void absorb(float& Nh, float& Nl, float tau, float& d
         Nh = __fadd_rn(s, lo);                            // renormalise (|lo| << |s|)
         Nl = __fsub_rn(lo, __fsub_rn(Nh, s));
     } else {
-        const float Nn = __fmul_rn(Nh, __expf(-tau));
+        // accurate exponential here: the hardware form's error grows with tau
+        // (argument rounding), and through thick gas it would accumulate along
+        // the ray
+        const float Nn = __fmul_rn(Nh, expf(-tau));
         d = __fsub_rn(Nh, Nn);                            // TwoSum(Nh, -Nn) = (d, r)
         const float bb = __fsub_rn(d, Nh);
         const float r = __fadd_rn(__fsub_rn(Nh, __fsub_rn(d, bb)), __fsub_rn(-Nn, bb));

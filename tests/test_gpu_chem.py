@@ -139,3 +139,30 @@ def test_rt_timestep_matches_oracle():
     assert np.isfinite(odtn) and np.isfinite(odti)
     assert abs(dtn / odtn - 1) < 1e-5, (dtn, odtn)
     assert abs(dti / odti - 1) < 1e-5, (dti, odti)
+
+
+def test_clump_test3_against_printed_results():
+    """The paper's Test 3 (Sec. 3.4) at full size, 15 Myr, graph-stepped: the
+    I-front along the line through the clump centre reaches x_HI = 0.5 near
+    r/L = 0.8; the photo-heated gas outside the clump is above 3e4 K, the gas
+    in the clump below 2e4 K; the shadow behind the clump stays neutral and
+    the thin gas in front is ionised."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))["test3_clump"]
+    w = W.clump_test3()
+    with P.Arc(w.n, w.box_cm, w.params()) as a:
+        a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
+        a.add_sources(w.src_pos, w.src_ndot)
+        for _ in range(w.nsteps):
+            a.step(w.dt_s)
+        x, _, _, T = a.get_fields()
+    axis = lambda f: 0.25 * (f[:, 63, 63] + f[:, 63, 64] + f[:, 64, 63] + f[:, 64, 64])
+    xa, Ta = axis(x), axis(T)
+    rL = (np.arange(w.n) + 0.5) / w.n
+    k = np.where((rL > 0.6) & (xa > 0.5))[0][0]
+    assert abs(rL[k] - gold["ifront_x_half_r_over_L"]) < 0.05, rL[k]
+    assert (Ta[(rL > 0.05) & (rL < 0.55)] > gold["T_outside_clump_above_K"]).all()
+    assert (Ta[(rL > 0.65) & (rL < 0.88)] < gold["T_inside_clump_below_K"]).all()
+    assert (xa[rL > 0.9] > 0.5).all()
+    assert (xa[(rL > 0.05) & (rL < 0.55)] < 1e-3).all()

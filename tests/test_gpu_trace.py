@@ -234,6 +234,12 @@ def test_geometric_correction_matches_oracle(seed):
             assert rel.max() <= 1e-3, (name, s, float(rel.max()), int(m.sum()))
 
 
+def test_clump_test3_geometry():
+    """The paper's Test 3 geometry (Sec. 3.4) at 64^3: a dense clump in thin
+    gas lit from the opposite face; trees and rates as the oracle's."""
+    check_pair(W.clump_test3(n=64), records=True)
+
+
 def test_autotune_picks_a_shape_and_keeps_results():
     """The autotuner times candidate launch shapes and keeps the fastest; the
     traced result does not depend on the shape it picked."""

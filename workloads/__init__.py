@@ -183,6 +183,31 @@ def thermal_128(seed: int = 0, n: int = 128, box_kpc: float = 6.6) -> Workload:
                     dt_s=0.5 * MYR, nsteps=100, z_compton=9.0, seed=seed)
 
 
+def clump_test3(n: int = 128, box_kpc: float = 6.6, dt_myr: float = 0.05, t_end_myr: float = 15.0) -> Workload:
+    """The paper's Test 3 (Sec. 3.4, after RT06): a dense hydrogen clump
+    (n = 0.04, 40 K, radius 0.8 kpc, centred at (97, 64, 64) of 128 cells) in
+    thin gas (n = 2e-4, 8000 K) of a 6.6 kpc box, lit by one point source of
+    3e51 photons/s opposite the clump (1e5 K blackbody in 3 groups).  The
+    source sits at the centre of the cell at (0, 64, 64) (0.87-cell shift);
+    pure hydrogen, no Compton term; 15 Myr.  At other n the geometry scales."""
+    grp = blackbody_groups(1e5)
+    s = n / 128.0
+    c = np.indices((n, n, n)).transpose(1, 2, 3, 0) + 0.5
+    centre = np.array([97.0, 64.0, 64.0]) * s
+    R = 0.8 / box_kpc * n
+    inside = ((c - centre) ** 2).sum(-1) < R * R
+    nH = np.where(inside, 0.04, 2e-4).astype(np.float32)
+    T = np.where(inside, 40.0, 8000.0).astype(np.float32)
+    x0 = 1.2e-3
+    xHI = np.full((n, n, n), 1.0 - x0, np.float32)
+    z = np.zeros((n, n, n), np.float32)
+    src = np.array([[0.5, 64.5 * s, 64.5 * s]])
+    return Workload(name=f"clump_test3_{n}", n=n, box_cm=box_kpc * KPC, Y=0.0, ngroups=3,
+                    E_group_eV=grp["E"], sigma=grp["sigma"], nH=nH, xHI=xHI, xHeI=z.copy(), xHeII=z.copy(),
+                    T=T, src_pos=src, src_ndot=(3e51 * grp["frac"])[None, :], dt_s=dt_myr * MYR,
+                    nsteps=int(round(t_end_myr / dt_myr)), z_compton=-1.0, seed=0)
+
+
 def gaussian_field_k3(n: int, rng: np.random.Generator) -> np.ndarray:
     """Unit-variance Gaussian random field with P(k) ~ k^-3 (k != 0, |k_i| <= n/2)."""
     w = rng.standard_normal((n, n, n))
