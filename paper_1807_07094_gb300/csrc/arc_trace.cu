@@ -215,9 +215,24 @@ __device__ float3 healpix_dir(int level, uint64_t pix) {
     int jp = (lon * nr + ix - iy + 1 + shift) >> 1;     // numerator is always even
     if (jp > 4 * ns) jp -= 4 * ns;
     if (jp < 1) jp += 4 * ns;
-    const float q = (float)(2 * jp - shift - 1) / (float)(4 * nr);   // longitude / pi
+    // longitude / pi = m / (4 nr), reduced exactly (in integers) to the
+    // nearest multiple of 1/2 plus a small offset, so that a component that
+    // is nearly zero keeps its relative accuracy: its absolute error would
+    // otherwise become a large relative error in 1/u, and the crossing of a
+    // plane the ray runs almost parallel to would move by ~1e-3 cells
+    const int m = 2 * jp - shift - 1;
+    const int half = 2 * nr;
+    const int k = (m + nr) / half;                      // nearest multiple of 1/2 (m >= 0)
+    const float qr = (float)(m - k * half) / (float)(4 * nr);   // |qr| <= 1/4
+    float s0, c0;
+    sincospif(qr, &s0, &c0);
     float sp, cp;
-    sincospif(q, &sp, &cp);
+    switch (k & 3) {
+        case 0: sp = s0; cp = c0; break;
+        case 1: sp = c0; cp = -s0; break;
+        case 2: sp = -s0; cp = -c0; break;
+        default: sp = -c0; cp = s0; break;
+    }
     return make_float3(sth * cp, sth * sp, z);
 }
 
