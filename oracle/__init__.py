@@ -23,7 +23,7 @@ _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liborc.so")
 
 MAXG = 4
-END_SPLIT, END_ESCAPE, END_TERM = 1, 2, 3
+END_SPLIT, END_ESCAPE, END_TERM, END_BLOCKED = 1, 2, 3, 4
 
 
 class OrcParams(C.Structure):
@@ -35,6 +35,11 @@ class OrcParams(C.Structure):
         ("isothermal", C.c_int), ("alpha_B_fixed", C.c_double), ("coll_ion", C.c_int),
         ("z_compton", C.c_double), ("geo_corr", C.c_int),
     ]
+
+
+class OrcTraceOpts(C.Structure):
+    _fields_ = [("corr_margin", C.c_void_p), ("r_start", C.c_void_p), ("r_thin_out", C.c_void_p),
+                ("thin_photons", C.c_void_p), ("open", C.c_void_p)]
 
 
 REC_DTYPE = np.dtype([("src", "<u4"), ("level", "<i4"), ("pix", "<u8"), ("visits", "<i4"),
@@ -111,6 +116,8 @@ def lib(path: Optional[str] = None):
         L.orc_trace.restype = C.c_int
         L.orc_trace_ex.argtypes = L.orc_trace.argtypes + [C.c_void_p]
         L.orc_trace_ex.restype = C.c_int
+        L.orc_trace_opt.argtypes = L.orc_trace.argtypes + [C.POINTER(OrcTraceOpts)]
+        L.orc_trace_opt.restype = C.c_int
         L.orc_chem.argtypes = [C.POINTER(OrcParams), C.c_int64, dp, dp, dp, dp, dp, dp, dp,
                                C.c_double, C.POINTER(C.c_int64)]
         L.orc_chem.restype = C.c_int
@@ -166,9 +173,15 @@ def r_split(params: dict, level: int) -> float:
 
 
 def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool = False,
-          rec_cap: int = 1 << 22, corr_margin: bool = False):
+          rec_cap: int = 1 << 22, corr_margin: bool = False, r_start=None, open_mask=None):
     """One RT pass.  Returns dict(gamma[3,n,n,n], heat[3,n,n,n], budget[3],
-    nseg, nrec, recs (structured array or None))."""
+    nseg, nrec, recs (structured array or None), corr_margin, r_thin[nsrc],
+    thin_photons).
+
+    r_start: per-source optically thin radius [cells] (Sec. 2.6): the thin
+    fill inside it and rays launched at it.  open_mask: [nsrc, 12*4^l_base]
+    booleans, False blocks that emitted ray (Sec. 2.2).  r_thin is always the
+    next thin radius measured by this pass."""
     p = make_params(params)
     n = p.n
     f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
@@ -183,10 +196,24 @@ def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool =
     nseg = C.c_int64(0)
     recs = np.zeros(rec_cap if records else 0, dtype=REC_DTYPE)
     cm = np.zeros(n ** 3 if corr_margin else 0)
-    rc = lib().orc_trace_ex(C.byref(p), _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII), nsrc,
-                            _dptr(pos), _dptr(ndot), _dptr(gamma), _dptr(heat), _dptr(budget),
-                            recs.ctypes.data if records else None, rec_cap if records else 0,
-                            C.byref(nrec), C.byref(nseg), cm.ctypes.data if corr_margin else None)
+    r_thin = np.zeros(nsrc)
+    thin = np.zeros(1)
+    o = OrcTraceOpts()
+    o.corr_margin = cm.ctypes.data if corr_margin else None
+    o.r_thin_out = r_thin.ctypes.data
+    o.thin_photons = thin.ctypes.data
+    if r_start is not None:
+        rs = f(r_start)
+        assert rs.size == nsrc
+        o.r_start = rs.ctypes.data
+    if open_mask is not None:
+        om = np.ascontiguousarray(np.asarray(open_mask, dtype=np.uint8).reshape(-1))
+        assert om.size == nsrc * 12 * 4 ** p.l_base
+        o.open = om.ctypes.data
+    rc = lib().orc_trace_opt(C.byref(p), _dptr(nH), _dptr(xHI), _dptr(xHeI), _dptr(xHeII), nsrc,
+                             _dptr(pos), _dptr(ndot), _dptr(gamma), _dptr(heat), _dptr(budget),
+                             recs.ctypes.data if records else None, rec_cap if records else 0,
+                             C.byref(nrec), C.byref(nseg), C.byref(o))
     if rc == -2:
         raise RuntimeError(f"oracle record buffer too small: {nrec.value} > {rec_cap}")
     if rc != 0:
@@ -194,7 +221,8 @@ def trace(params: dict, nH, xHI, xHeI, xHeII, src_pos, src_ndot, records: bool =
     return dict(gamma=gamma.reshape(3, n, n, n), heat=heat.reshape(3, n, n, n), budget=budget,
                 nseg=int(nseg.value), nrec=int(nrec.value),
                 recs=recs[: nrec.value] if records else None,
-                corr_margin=cm.reshape(n, n, n) if corr_margin else None)
+                corr_margin=cm.reshape(n, n, n) if corr_margin else None,
+                r_thin=r_thin, thin_photons=float(thin[0]))
 
 
 def chem(params: dict, nH, xHI, xHeI, xHeII, T, gamma, heat, dt: float, min_sub: int = 0):

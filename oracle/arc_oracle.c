@@ -169,7 +169,13 @@ typedef struct {
     double thr_base;      /* term_frac * photons of one ray at l_base */
     double* cmargin;      /* optional: per cell, smallest face-tie margin of the
                              geometric corrections that touched it [cells] */
+    /* Sec. 2.6: a ray's length while its optical depth in the softest group
+     * is below 0.1; the minimum over the current source's rays */
+    int soft;             /* softest group (lowest photon energy) */
+    double rthin;         /* running minimum for the current source [cells] */
 } tctx;
+
+#define THIN_TAU 0.1      /* Sec. 2.6 */
 
 /* absorber densities n_HI, n_HeI, n_HeII of a cell [cm^-3] (Sec. 2.3) */
 static void absorbers(const tctx* c, int64_t idx, double ns[3]) {
@@ -196,7 +202,9 @@ static void deposit(tctx* c, int64_t idx, int b, double A, double kappa_b) {
     }
 }
 
-static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double* Nin) {
+/* tau0: optical depth in the softest group accumulated from where the ray's
+ * ancestors started (Sec. 2.6); only the thin radius uses it. */
+static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double* Nin, double tau0) {
     const orc_params* p = c->p;
     const int G = p->ngroups, n = c->n;
     double N[ORC_MAXG];
@@ -222,7 +230,15 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
 
     if (cell[0] < 0 || cell[0] >= n || cell[1] < 0 || cell[1] >= n || cell[2] < 0 || cell[2] >= n) {
         for (int b = 0; b < G; b++) c->escaped += N[b];
+        if (tau0 < THIN_TAU) c->rthin = fmin(c->rthin, r0);
         end = ORC_END_ESCAPE;
+        goto record;
+    }
+    /* a ray that starts at or beyond its split distance (rays launched at the
+     * optically thin radius, Sec. 2.6) splits at once without a segment */
+    if (isfinite(r_stop)) exitm = fmin(exitm, fabs(r0 - r_stop));
+    if (r0 >= r_stop) {
+        end = ORC_END_SPLIT;
         goto record;
     }
     for (;;) {
@@ -330,6 +346,15 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
                 }
             }
         }
+        /* Sec. 2.6: where the softest group's optical depth reaches 0.1 */
+        {
+            double ks = 0.0;
+            for (int s = 0; s < 3; s++) ks += p->sigma[s][c->soft] * ns[s];
+            const double dt0 = ks * L;
+            if (tau0 < THIN_TAU && tau0 + dt0 >= THIN_TAU)
+                c->rthin = fmin(c->rthin, r + (THIN_TAU - tau0) / (ks * c->dx));
+            tau0 += dt0;
+        }
         visits++;
         c->nseg++;
         r = r1;
@@ -347,6 +372,7 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
                     N[b] = 0.0;
                 }
             }
+            if (tau0 < THIN_TAU) c->rthin = fmin(c->rthin, r);
             end = ORC_END_TERM;
             break;
         }
@@ -365,6 +391,7 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
             for (int a = 0; a < 3; a++)
                 if (a != ax) geo = fmin(geo, fabs(tn[a] - t));
             for (int b = 0; b < G; b++) c->escaped += N[b];
+            if (tau0 < THIN_TAU) c->rthin = fmin(c->rthin, r);
             end = ORC_END_ESCAPE;
             break;
         }
@@ -393,7 +420,7 @@ record:
          * photons each (Sec. 2.1 step iii.c) */
         double Nc[ORC_MAXG];
         for (int b = 0; b < G; b++) Nc[b] = N[b] / 4.0;
-        for (int k = 0; k < 4; k++) trace_ray(c, level + 1, 4 * pix + (uint64_t)k, r, Nc);
+        for (int k = 0; k < 4; k++) trace_ray(c, level + 1, 4 * pix + (uint64_t)k, r, Nc, tau0);
     }
 }
 
@@ -411,15 +438,64 @@ int orc_trace_ex(const orc_params* p, const double* nH, const double* xHI,
                  int nsrc, const double* pos, const double* ndot,
                  double* gamma, double* heat, double* budget,
                  orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg, double* corr_margin) {
+    orc_trace_opts o;
+    memset(&o, 0, sizeof o);
+    o.corr_margin = corr_margin;
+    return orc_trace_opt(p, nH, xHI, xHeI, xHeII, nsrc, pos, ndot, gamma, heat, budget, recs, rec_cap, nrec,
+                         nseg, &o);
+}
+
+/* Sec. 2.6, step 3: every cell whose centre lies within R of the source is
+ * taken as exposed without absorption; the thin limit of Eq. (ion) for the
+ * rays crossing it is S_b sigma_{s,b} / (4 pi r^2) per absorber, i.e. the cell
+ * absorbs S_b kappa_b V / (4 pi r^2) photons per group (kappa_b per length).
+ * r is the centre's distance from the source, floored at half a cell (the
+ * paper gives no value in the source's own cell, where 1/r^2 diverges).
+ * Returns the photons deposited. */
+static double thin_fill(tctx* c, const double* o, double R, const double* S) {
+    const orc_params* p = c->p;
+    const int n = c->n, G = p->ngroups;
+    double tot = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) {
+                const double dx = i + 0.5 - o[0], dy = j + 0.5 - o[1], dz = k + 0.5 - o[2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < R * R)) continue;
+                const double rr = r2 > 0.25 ? r2 : 0.25;
+                const int64_t idx = ((int64_t)i * n + j) * n + k;
+                double ns[3];
+                absorbers(c, idx, ns);
+                for (int b = 0; b < G; b++) {
+                    double kb = 0.0;
+                    for (int s = 0; s < 3; s++) kb += p->sigma[s][b] * ns[s];
+                    const double kap = kb * c->dx;   /* per cell length */
+                    const double A = S[b] * kap / (4.0 * PI * rr);
+                    if (A > 0.0) {
+                        deposit(c, idx, b, A, kap);
+                        tot += A;
+                    }
+                }
+            }
+    return tot;
+}
+
+int orc_trace_opt(const orc_params* p, const double* nH, const double* xHI,
+                  const double* xHeI, const double* xHeII,
+                  int nsrc, const double* pos, const double* ndot,
+                  double* gamma, double* heat, double* budget,
+                  orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg,
+                  const orc_trace_opts* opt) {
     if (!p || p->n <= 0 || p->ngroups < 1 || p->ngroups > ORC_MAXG || p->l_base < 1 ||
-        p->l_max < p->l_base || p->phi <= 0.0 || nsrc < 0)
+        p->l_max < p->l_base || p->phi <= 0.0 || nsrc < 0 || !opt)
         return -1;
+    if (opt->open && opt->r_start) return -1;   /* masks and the thin region do not combine */
     tctx c;
     memset(&c, 0, sizeof c);
     c.p = p;
-    c.cmargin = corr_margin;
-    if (corr_margin)
-        for (int64_t i = 0; i < (int64_t)p->n * p->n * p->n; i++) corr_margin[i] = INFINITY;
+    c.cmargin = opt->corr_margin;
+    if (c.cmargin)
+        for (int64_t i = 0; i < (int64_t)p->n * p->n * p->n; i++) c.cmargin[i] = INFINITY;
     c.nH = nH;
     c.xHI = xHI;
     c.xHeI = xHeI;
@@ -432,30 +508,59 @@ int orc_trace_ex(const orc_params* p, const double* nH, const double* xHI,
     c.heat = heat;
     c.recs = recs;
     c.rec_cap = recs ? rec_cap : 0;
+    c.soft = 0;
+    for (int b = 1; b < p->ngroups; b++)
+        if (p->E_group_eV[b] < p->E_group_eV[c.soft]) c.soft = b;
     const int64_t n3 = (int64_t)p->n * p->n * p->n;
     memset(gamma, 0, sizeof(double) * 3 * n3);   /* Sec. 2.1 step i */
     memset(heat, 0, sizeof(double) * 3 * n3);
     const int G = p->ngroups;
     const double nrays = 12.0 * pow(4.0, p->l_base);
-    double emitted = 0.0;
+    double launched = 0.0, thin = 0.0;
     for (int s = 0; s < nsrc; s++) {
-        double N0[ORC_MAXG], tot = 0.0;
+        double N0[ORC_MAXG], S[ORC_MAXG], tot = 0.0;
         for (int b = 0; b < G; b++) {
-            N0[b] = ndot[(int64_t)s * G + b] / nrays;   /* equal share per packet */
-            tot += ndot[(int64_t)s * G + b];
+            S[b] = ndot[(int64_t)s * G + b];
+            N0[b] = S[b] / nrays;   /* equal share per packet */
+            tot += S[b];
         }
+        if (opt->r_thin_out) opt->r_thin_out[s] = 0.0;
         if (!(tot > 0.0)) continue;
-        emitted += tot;
         c.o = &pos[3 * (int64_t)s];
         c.isrc = (uint32_t)s;
         c.thr_base = p->term_frac * tot / nrays;
-        for (uint64_t q = 0; q < (uint64_t)nrays; q++) trace_ray(&c, p->l_base, q, 0.0, N0);
+        c.rthin = INFINITY;
+        const double R = opt->r_start ? opt->r_start[s] : 0.0;
+        if (R > 0.0) thin += thin_fill(&c, c.o, R, S);
+        for (uint64_t q = 0; q < (uint64_t)nrays; q++) {
+            if (opt->open && !opt->open[(int64_t)s * (int64_t)nrays + (int64_t)q]) {
+                /* anisotropic escape (Sec. 2.2): this direction emits nothing */
+                if (c.recs && c.nrec < c.rec_cap) {
+                    orc_ray_rec* r = &c.recs[c.nrec];
+                    memset(r, 0, sizeof *r);
+                    r->src = c.isrc;
+                    r->level = p->l_base;
+                    r->pix = q;
+                    r->end = ORC_END_BLOCKED;
+                    r->r0 = r->r1 = R;
+                    r->geo_margin = r->term_margin = r->exit_margin = INFINITY;
+                } else if (c.recs) {
+                    c.overflow = 1;
+                }
+                c.nrec++;
+                continue;
+            }
+            launched += tot / nrays;
+            trace_ray(&c, p->l_base, q, R, N0, 0.0);
+        }
+        if (opt->r_thin_out) opt->r_thin_out[s] = isfinite(c.rthin) ? c.rthin : 0.0;
     }
     if (budget) {
-        budget[0] = emitted;
+        budget[0] = launched;
         budget[1] = c.absorbed;
         budget[2] = c.escaped;
     }
+    if (opt->thin_photons) *opt->thin_photons = thin;
     if (nrec) *nrec = c.nrec;
     if (nseg) *nseg = c.nseg;
     return c.overflow ? -2 : 0;

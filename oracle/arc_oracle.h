@@ -9,8 +9,12 @@
  * Sections of the paper it follows (Hartley & Ricotti, "ARC"):
  *   Sec. 2.1  program design: 48 HEALPix level-1 packets per source, split
  *             into 4 children at the next level, termination.
+ *   Sec. 2.2  anisotropic escape: emitted rays of a source may be blocked.
  *   Sec. 2.4  photon transmission: cell-by-cell stepping to the next X/Y/Z
  *             boundary, Eq. (ion) photon-conserving absorption.
+ *   Sec. 2.5  geometric correction f_c and its secondary f'_c.
+ *   Sec. 2.6  optically thin approximation: radius R_{tau<0.1}, the thin
+ *             fill inside it, rays launched at R.
  *   Sec. 2.3  grid data: electron density.
  *   Sec. 2.7  ionisation calculation: Eq. (diffeq), Eq. (anninos), the
  *             sub-cycle step limiter with epsilon = 0.1.
@@ -51,6 +55,7 @@ typedef struct {
 #define ORC_END_SPLIT 1
 #define ORC_END_ESCAPE 2
 #define ORC_END_TERM 3
+#define ORC_END_BLOCKED 4   /* a masked emission direction: no photons, no cells */
 
 typedef struct {
     uint32_t src;        /* source index                                         */
@@ -97,6 +102,29 @@ int orc_trace_ex(const orc_params* p, const double* nH, const double* xHI,
                  int nsrc, const double* pos, const double* ndot,
                  double* gamma, double* heat, double* budget,
                  orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg, double* corr_margin);
+
+/* Options of orc_trace_opt (each may be NULL / 0). */
+typedef struct {
+    double* corr_margin;        /* as for orc_trace_ex                                 */
+    const double* r_start;      /* nsrc: optically thin radius R per source [cells]
+                                   (Sec. 2.6): cells with centres within R get the
+                                   thin-limit rate, rays start at distance R       */
+    double* r_thin_out;         /* nsrc: min over the source's rays of the length
+                                   while the softest group's optical depth, counted
+                                   from the ray's start, is below 0.1 (0 if none)  */
+    double* thin_photons;       /* photons/s deposited by the thin fill               */
+    const unsigned char* open;  /* nsrc x 12*4^l_base: 0 blocks that emitted ray
+                                   (anisotropic escape, Sec. 2.2); not with r_start */
+} orc_trace_opts;
+
+/* orc_trace with options.  budget[0] counts the photons of emitted (open)
+ * rays only; the thin fill's photons are not part of budget[1]. */
+int orc_trace_opt(const orc_params* p, const double* nH, const double* xHI,
+                  const double* xHeI, const double* xHeII,
+                  int nsrc, const double* pos, const double* ndot,
+                  double* gamma, double* heat, double* budget,
+                  orc_ray_rec* recs, int64_t rec_cap, int64_t* nrec, int64_t* nseg,
+                  const orc_trace_opts* opt);
 
 /*
  * Sub-cycled chemistry / energy update of ncell cells over dt seconds

@@ -13,6 +13,7 @@ import pytest
 import oracle
 import test_oracle_chem as CH
 import test_oracle_healpix as HP
+import test_oracle_thin as TH
 import test_oracle_trace as TR
 
 # (name, original text, mutated text)
@@ -35,8 +36,9 @@ MUTANTS = [
     ("threshold not scaled by level", "const double thr = c->thr_base / pow(4.0, level - p->l_base);",
      "const double thr = c->thr_base;"),
     ("heating sign of edge", "rate * (p->E_group_eV[b] - E_S[s]) * EVERG", "rate * (p->E_group_eV[b] + E_S[s]) * EVERG"),
-    ("escape not booked", "for (int b = 0; b < G; b++) c->escaped += N[b];\n            end = ORC_END_ESCAPE;\n            break;",
-     "end = ORC_END_ESCAPE;\n            break;"),
+    ("escape not booked",
+     "for (int b = 0; b < G; b++) c->escaped += N[b];\n            if (tau0 < THIN_TAU) c->rthin = fmin(c->rthin, r);",
+     "if (tau0 < THIN_TAU) c->rthin = fmin(c->rthin, r);"),
     ("recombination on HI", "const double DH = r[0] * ne * nH;", "const double DH = r[0] * ne * nHI;"),
     ("HeI source from HeI", "const double C1 = G1 + r[4] * ne, D1 = r[1] * ne * nHeII;",
      "const double C1 = G1 + r[4] * ne, D1 = r[1] * ne * nHeI;"),
@@ -52,6 +54,19 @@ MUTANTS = [
      "else if (u[a] < 0.0) tn[a] = ((double)cell[a] - 1.0 - o[a]) / u[a];"),
     ("nearest plane picks the largest", "if (tn[2] < tn[ax]) ax = 2;", "if (tn[2] > tn[ax]) ax = 2;"),
     ("segment from the cell start", "double ds = r1 - r;", "double ds = r1 - r0;"),
+    # optically thin approximation (Sec. 2.6) and emission masks (Sec. 2.2)
+    ("thin depth 0.2", "#define THIN_TAU 0.1 ", "#define THIN_TAU 0.2 "),
+    ("crossing without cell length", "r + (THIN_TAU - tau0) / (ks * c->dx)", "r + (THIN_TAU - tau0) / ks"),
+    ("softest group is the hardest", "if (p->E_group_eV[b] < p->E_group_eV[c.soft]) c.soft = b;",
+     "if (p->E_group_eV[b] > p->E_group_eV[c.soft]) c.soft = b;"),
+    ("children restart the depth", "trace_ray(c, level + 1, 4 * pix + (uint64_t)k, r, Nc, tau0);",
+     "trace_ray(c, level + 1, 4 * pix + (uint64_t)k, r, Nc, 0.0);"),
+    ("fill without 4 pi", "const double A = S[b] * kap / (4.0 * PI * rr);", "const double A = S[b] * kap / rr;"),
+    ("fill falls as 1/r", "const double rr = r2 > 0.25 ? r2 : 0.25;", "const double rr = sqrt(r2 > 0.25 ? r2 : 0.25);"),
+    ("rays start at the source", "trace_ray(&c, p->l_base, q, R, N0, 0.0);", "trace_ray(&c, p->l_base, q, 0.0, N0, 0.0);"),
+    ("no split at the start", "if (r0 >= r_stop) {", "if (r0 > 1e30) {"),
+    ("mask ignores the source", "opt->open[(int64_t)s * (int64_t)nrays + (int64_t)q]", "opt->open[(int64_t)q]"),
+    ("blocked rays still emit", "c.nrec++;\n                continue;", "c.nrec++;"),
 ]
 
 # fast pins first; a mutant is killed at the first failure
@@ -76,6 +91,13 @@ PINS = [
     TR.test_termination_distance_in_uniform_medium,
     TR.test_rays_per_face_at_split_equals_phi,
     TR.test_optically_thin_shells,
+    lambda: TH.test_thin_radius_uniform_closed_form((10.25, 19.5, 14.75), 0.02),
+    TH.test_thin_radius_uses_softest_group,
+    lambda: TH.test_thin_start_tree_and_escape_radius((9.25, 20.5, 13.75), 3.1),
+    lambda: TH.test_thin_trace_beyond_radius_is_the_plain_one_unattenuated(7.5),
+    TH.test_thin_fill_matches_traced_small_tau_limit,
+    TH.test_complementary_masks_add_up,
+    lambda: TH.test_single_open_pixel_lights_its_cone(22),
 ]
 
 
