@@ -380,6 +380,66 @@ def run_memops():
     return r.returncode
 
 
+def run_thin(args):
+    """The optically thin approximation (Sec. 2.6) on the benchmark field: every
+    source in an ionised sphere of args.thin cells, traced with the
+    approximation off and on (the radii of the first trace in place), K traces
+    each timed with CUDA events on the context stream.  Prints one JSON line."""
+    import torch
+    import paper_1807_07094_gb300 as P
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    w = W.cosmic_256()
+    xs = W.ionised_bubbles(w, args.thin)
+    out = {}
+    for mode in ("plain", "thin"):
+        p = dict(w.params(), thin_approx=1 if mode == "thin" else 0)
+        stream = torch.cuda.Stream()
+        with P.Arc(w.n, w.box_cm, p, stream=stream.cuda_stream) as a:
+            a.set_fields(w.nH, *xs, w.T)
+            a.add_sources(w.src_pos, w.src_ndot)
+            a.autotune(max_sources=min(100, w.nsrc), reps=1)
+            for _ in range(args.warmup):           # the first trace measures the radii
+                a.trace(w.dt_s, budget=True)
+            radii = a.thin_radii(len(w.src_pos))[0] if mode == "thin" else None
+            if mode == "thin":
+                a.set_thin_radii(radii)            # hold the radii fixed while timing
+            torch.cuda.synchronize()
+            ms, segs = [], []
+            for _ in range(args.steps):
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                _, _, b = a.trace(w.dt_s, budget=True)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+                segs.append(a.stats()["segments"])
+                if mode == "thin":
+                    a.set_thin_radii(radii)
+            rec = dict(ms=float(np.median(ms)), segments=int(np.median(segs)), budget_closure=float(
+                abs(b[0] - b[1] - b[2]) / b[0]))
+            if mode == "thin":
+                rec["mean_radius_cells"] = float(radii.mean())
+                rec["thin_fill_photons"] = a.thin_radii(len(w.src_pos))[1]
+            out[mode] = rec
+    line = {
+        "metric": "RT trace time with the optically thin approximation (Sec. 2.6)",
+        "value": out["thin"]["ms"], "unit": "ms", "higher_is_better": False,
+        "plain_ms": out["plain"]["ms"], "speedup": out["plain"]["ms"] / out["thin"]["ms"],
+        "segments_plain": out["plain"]["segments"], "segments_thin": out["thin"]["segments"],
+        "detail": out, "steps": args.steps, "warmup": args.warmup, "n_gpus": 1, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"cosmic_256 with an ionised sphere of {args.thin} cells around each source "
+                               "(x_HI = x_HeI = 1e-4, x_HeII = 0.05 inside)"},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,11 +456,16 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-ODE chemistry comparison")
     ap.add_argument("--memops", action="store_true",
                     help="measure the memory-operation ceilings of the tracer's access pattern and exit")
+    ap.add_argument("--thin", type=float, default=0.0,
+                    help="time traces with and without the optically thin approximation on the benchmark "
+                         "field with ionised spheres of this radius [cells] around the sources, and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.memops:
         return run_memops()
+    if args.thin > 0:
+        return run_thin(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -92,6 +92,18 @@ typedef struct {
                                              face, 1 - f_c (f_c = 1/2 + D_edge / L) of
                                              its absorbed photons go to the neighbour
                                              across that face; 0: off                  */
+    int thin_approx;                      /* 1: optically thin approximation (Sec. 2.6):
+                                             every source carries a radius R (0 at
+                                             first); cells whose centre lies within R
+                                             take the thin limit of Eq. (ion),
+                                             S_b sigma_{s,b} / (4 pi r^2) per absorber
+                                             (r from the source to the cell centre,
+                                             at least half a cell), rays start at
+                                             distance R, and each trace sets the next
+                                             R to the minimum over the source's rays of
+                                             the length while the optical depth of
+                                             group 0 (which must be the softest) is
+                                             below 0.1; 0: off                         */
 } arc_params;
 
 /* Counters of the last arc_trace / arc_chem_update (arc_stats synchronises). */
@@ -119,10 +131,13 @@ typedef struct {
 typedef struct {
     uint32_t src;            /* source index in the order sources were added           */
     uint8_t level;           /* HEALPix level                                          */
-    uint8_t end;             /* 1 split, 2 escaped, 3 terminated                       */
+    uint8_t end;             /* 1 split, 2 escaped, 3 terminated, 4 blocked by the
+                                source's emission mask (no photons, no cells)         */
     uint16_t pad;
     uint64_t pix;            /* nested pixel index at that level                       */
-    uint32_t visits;         /* cell segments traced, zero-length ones included       */
+    uint32_t visits;         /* cell segments traced, zero-length ones included; 0 for
+                                a ray that starts at or beyond its split distance
+                                (thin_approx) and splits at once                     */
     float r1;                /* distance from the source where the ray ended [cells]  */
 } arc_ray_rec;
 
@@ -172,9 +187,11 @@ arc_status arc_clear_sources(arc_ctx* ctx);
  *   heat    receives a device pointer to 3*n^3 photoheating rates per
  *           absorber [erg/s]; may be NULL
  *   budget  NULL, or host double[4] receiving photons over dt:
- *           [0] launched into rays, [1] absorbed in cells, [2] escaped from
- *           the box, [3] emitted by the sources (FP64 input sum).  [0] differs
- *           from [3] only by the FP32 rounding of each ray's initial share.
+ *           [0] launched into rays, [1] absorbed in cells from the rays, [2]
+ *           escaped from the box, [3] emitted by the sources (FP64 input sum).
+ *           [0] differs from [3] by the FP32 rounding of each ray's initial
+ *           share and by the rays an emission mask blocks.  The photons of the
+ *           thin fill (thin_approx) are in no entry: see arc_get_thin_radii.
  * With budget != NULL the call synchronises and returns ARC_E_BUDGET if
  * |launched - absorbed - escaped| > 1e-9 launched, ARC_E_TIMEOUT or
  * ARC_E_OVERFLOW if the tracer recorded such an error.
@@ -326,6 +343,32 @@ arc_status arc_set_surrogate(arc_ctx* ctx, const float* params, const float* nor
 
 /* Training.  A trainer holds FP32 master weights, AdamW moments and the
  * activations of one batch of up to max_batch samples (a multiple of 16). */
+/*
+ * arc_set_emission_mask -- anisotropic escape (Sec. 2.2): each source emits
+ * its mean per-ray share on the open rays only and nothing on the others.
+ *   open   nsrc * 12*4^l_base bytes, source-major in the order sources were
+ *          added, ray index = nested HEALPix pixel at level l_base; nonzero =
+ *          open.  NULL or count 0 removes the mask.
+ *   count  number of bytes in open
+ * Copied.  Adding or clearing sources removes the mask.  Returns
+ * ARC_E_INVALID for a count that does not match the sources, or when
+ * thin_approx is on (the two do not combine).
+ */
+arc_status arc_set_emission_mask(arc_ctx* ctx, const uint8_t* open, int64_t count);
+
+/*
+ * arc_set_thin_radii / arc_get_thin_radii -- the optically thin radius R of
+ * each source (Sec. 2.6; thin_approx only, else ARC_E_STATE), in grid cells
+ * and in the order sources were added.  A trace uses the current radii and
+ * then replaces them with the ones it measured.  Adding or clearing sources
+ * sets every radius to 0.  set: nsrc must equal the sources added, radii
+ * finite and >= 0 (ARC_E_INVALID otherwise); synchronises.  get: radii
+ * (may be NULL) receives them; thin_photons (may be NULL) the photons the
+ * thin fill deposited during the last trace, over its dt; synchronises.
+ */
+arc_status arc_set_thin_radii(arc_ctx* ctx, const double* radii, int nsrc);
+arc_status arc_get_thin_radii(arc_ctx* ctx, double* radii, int nsrc, double* thin_photons);
+
 typedef struct arc_mlp_trainer arc_mlp_trainer;
 arc_status arc_mlp_trainer_create(arc_mlp_trainer** out, int max_batch, void* stream);
 /* copy in parameters (host, ARC_MLP_NPARAMS) and reset the AdamW state */

@@ -46,7 +46,7 @@ class ArcParams(C.Structure):
         ("l_base", C.c_int), ("l_max", C.c_int), ("term_frac", C.c_double),
         ("eps_sub", C.c_double), ("x_fp64", C.c_double), ("isothermal", C.c_int),
         ("alpha_B_fixed", C.c_double), ("coll_ion", C.c_int), ("z_compton", C.c_double),
-        ("geo_correction", C.c_int),
+        ("geo_correction", C.c_int), ("thin_approx", C.c_int),
     ]
 
 
@@ -104,6 +104,9 @@ _SIGS = {
     "arc_mlp_features": ([C.c_void_p] * 7 + [C.c_double, C.c_longlong, C.c_void_p, C.c_void_p], C.c_int),
     "arc_rt_timestep": ([C.c_void_p, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "arc_mlp_targets": ([C.c_void_p] * 8 + [C.c_double, C.c_longlong, C.c_void_p], C.c_int),
+    "arc_set_emission_mask": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
+    "arc_set_thin_radii": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "arc_get_thin_radii": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
 }
 
 MLP_NPARAMS = 9412
@@ -150,6 +153,7 @@ def make_params(d: dict) -> ArcParams:
     for k in ("l_base", "l_max", "isothermal", "coll_ion"):
         setattr(p, k, int(d[k]))
     p.geo_correction = int(d.get("geo_corr", 0))
+    p.thin_approx = int(d.get("thin_approx", 0))
     return p
 
 
@@ -509,6 +513,28 @@ class Arc:
         a, b = C.c_double(), C.c_double()
         _check(self.ctx, load().arc_rt_timestep(C.c_void_p(self.ctx), float(eps), C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def set_emission_mask(self, open_mask=None):
+        """Anisotropic escape (Sec. 2.2): open_mask [nsrc, 12*4^l_base] booleans
+        in the order sources were added (False blocks that emitted ray); None
+        removes the mask."""
+        if open_mask is None:
+            _check(self.ctx, load().arc_set_emission_mask(C.c_void_p(self.ctx), None, 0))
+            return
+        m = np.ascontiguousarray(np.asarray(open_mask, dtype=np.uint8).reshape(-1))
+        _check(self.ctx, load().arc_set_emission_mask(C.c_void_p(self.ctx), m.ctypes.data, m.size))
+
+    def set_thin_radii(self, radii):
+        """Optically thin radius per source [cells] (Sec. 2.6, thin_approx)."""
+        r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
+        _check(self.ctx, load().arc_set_thin_radii(C.c_void_p(self.ctx), r.ctypes.data, r.size))
+
+    def thin_radii(self, nsrc: int):
+        """(radii [nsrc] the last trace measured, photons of its thin fill over dt)."""
+        r = np.zeros(nsrc)
+        t = C.c_double()
+        _check(self.ctx, load().arc_get_thin_radii(C.c_void_p(self.ctx), r.ctypes.data, nsrc, C.byref(t)))
+        return r, t.value
 
     def mlp_targets(self, nH, x0, T0, gamma, heat, x1, T1, dt: float, Y):
         arc_mlp_targets(self.ctx, nH, x0, T0, gamma, heat, x1, T1, dt, Y)

@@ -32,6 +32,7 @@ struct Scalars {
     unsigned int pad0;
     double escaped;
     double rounding;
+    double thin;                           // photons of the optically thin fill (Sec. 2.6)
     unsigned long long counters[CNT_ALL];
     unsigned long long nrec;
     double budget_out[2];
@@ -70,6 +71,17 @@ struct arc_ctx {
     double emitted_rate = 0.0;    // photons/s of the sources (FP64 input sum)
     Entry* seeds = nullptr;
     int seeds_cap = 0, nseeds = 0;
+    std::vector<uint32_t> dev_ids;   // device source order -> caller's index
+    // optically thin approximation (Sec. 2.6): radius per device source and
+    // the candidates the running trace measures (dsrc_cap entries each)
+    float* rthin = nullptr;
+    float* rnext = nullptr;
+    double last_dt = 0.0;
+    // anisotropic escape (Sec. 2.2): caller's mask (caller order) and its copy
+    // in device source order
+    std::vector<uint8_t> hopen;
+    uint8_t* dopen = nullptr;
+    size_t dopen_cap = 0;
     // dynamic queue
     Entry* qdata = nullptr;
     unsigned long long* qseq = nullptr;
@@ -143,6 +155,11 @@ arc_status check_params(arc_ctx* c, const arc_grid* g, const arc_params* p) {
     if (p->l_base < 1 || p->l_base > 6) return fail(c, ARC_E_INVALID, "l_base outside 1..6");
     if (p->geo_correction != 0 && p->geo_correction != 1)
         return fail(c, ARC_E_INVALID, "geo_correction must be 0 or 1");
+    if (p->thin_approx != 0 && p->thin_approx != 1) return fail(c, ARC_E_INVALID, "thin_approx must be 0 or 1");
+    if (p->thin_approx)
+        for (int b = 1; b < p->ngroups; ++b)
+            if (p->E_group_eV[b] < p->E_group_eV[0])
+                return fail(c, ARC_E_INVALID, "thin_approx needs group 0 to be the softest");
     if (p->l_max < p->l_base || p->l_max > ARC_MAX_LEVEL)
         return fail(c, ARC_E_INVALID, "l_max outside l_base..%d", ARC_MAX_LEVEL);
     if (!(p->term_frac > 0 && p->term_frac < 1)) return fail(c, ARC_E_INVALID, "term_frac outside (0,1)");
@@ -184,15 +201,28 @@ arc_status upload_sources(arc_ctx* c) {
                      [](const HostSource* a, const HostSource* b) { return a->total > b->total; });
     const int G = c->p.ngroups;
     const double nrays = 12.0 * pow(4.0, c->p.l_base);
+    const int nbase = 12 << (2 * c->p.l_base);
+    const bool masked = !c->hopen.empty();
     std::vector<SourceDev> h(act.size());
+    std::vector<uint8_t> dmask(masked ? act.size() * (size_t)nbase : 0);
+    c->dev_ids.resize(act.size());
     double launched = 0.0, emitted = 0.0;
     for (size_t i = 0; i < act.size(); ++i) {
         const HostSource& s = *act[i];
+        int open = nbase;
+        if (masked) {
+            open = 0;
+            for (int q = 0; q < nbase; ++q) {
+                const uint8_t v = c->hopen[(size_t)s.id * nbase + q] ? 1 : 0;
+                dmask[i * (size_t)nbase + q] = v;
+                open += v;
+            }
+        }
         float N0[ARC_MAX_GROUPS] = {0.f, 0.f, 0.f, 0.f};
         double tot = 0.0;
         for (int b = 0; b < G; ++b) {
             N0[b] = (float)(s.ndot[b] / PHOT_UNIT / nrays);
-            launched += (double)N0[b] * nrays * PHOT_UNIT;
+            launched += (double)N0[b] * open * PHOT_UNIT;   // blocked rays carry nothing
             tot += (double)N0[b];
         }
         emitted += s.total;
@@ -200,16 +230,30 @@ arc_status upload_sources(arc_ctx* c) {
                                    (float)(c->p.term_frac * tot));
         h[i].N0 = make_float4(N0[0], N0[1], N0[2], N0[3]);
         h[i].id = s.id;
-        h[i].pad[0] = h[i].pad[1] = h[i].pad[2] = 0;
+        h[i].cthr0 = N0[0] > 0.f ? (float)((double)N0[0] * exp(-0.1)) : 0.f;   // Sec. 2.6
+        h[i].pad[0] = h[i].pad[1] = 0;
+        c->dev_ids[i] = s.id;
     }
     const int ns = (int)act.size();
     const int per_src = 3 << (2 * c->p.l_base);
     if (ns > c->dsrc_cap) {
         dfree(c->dsrc);
+        dfree(c->rthin);
+        dfree(c->rnext);
         c->dsrc = nullptr;
+        c->rthin = c->rnext = nullptr;
         const int cap = std::max(ns, 16);
         CK(dalloc(&c->dsrc, cap));
+        CK(dalloc(&c->rthin, cap));
+        CK(dalloc(&c->rnext, cap));
         c->dsrc_cap = cap;
+        c->graph_valid = false;
+    }
+    if (masked && dmask.size() > c->dopen_cap) {
+        dfree(c->dopen);
+        c->dopen = nullptr;
+        CK(dalloc(&c->dopen, dmask.size()));
+        c->dopen_cap = dmask.size();
         c->graph_valid = false;
     }
     if ((long long)ns * per_src > c->seeds_cap) {
@@ -223,8 +267,12 @@ arc_status upload_sources(arc_ctx* c) {
     }
     if (ns > 0) {
         CK(cudaMemcpyAsync(c->dsrc, h.data(), ns * sizeof(SourceDev), cudaMemcpyHostToDevice, c->stream));
+        if (masked)
+            CK(cudaMemcpyAsync(c->dopen, dmask.data(), dmask.size(), cudaMemcpyHostToDevice, c->stream));
+        // a new source table starts every optically thin radius at 0
+        CK(cudaMemsetAsync(c->rthin, 0, ns * sizeof(float), c->stream));
         CK(launch_make_seeds(c->dsrc, ns, c->p.l_base, c->seeds, c->stream));
-        CK(cudaStreamSynchronize(c->stream));   // h goes out of scope
+        CK(cudaStreamSynchronize(c->stream));   // h and dmask go out of scope
     }
     if (ns != c->nsrc_dev) c->graph_valid = false;
     c->nsrc_dev = ns;
@@ -263,6 +311,10 @@ TraceArgs trace_args(arc_ctx* c) {
         a.pixw[l] = (float)sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * l)));   // Omega_l = 4 pi / (12 4^l)
     }
     a.geo_corr = c->p.geo_correction ? 1 : 0;
+    a.open = c->hopen.empty() ? nullptr : c->dopen;
+    a.nbase = 12 << (2 * c->p.l_base);
+    a.rnext = c->p.thin_approx ? c->rnext : nullptr;
+    a.thin = &c->scal->thin;
     a.seeds = c->seeds;
     a.nseeds = c->nseeds;
     a.seed_head = &c->scal->seed_head;
@@ -291,7 +343,9 @@ int trace_grid(arc_ctx* c) {
     if (per_sm <= 0) {
         int occ = 0;
         const int smem = trace_smem_bytes(c->block, c->stack_log2);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(c->p.ngroups), c->block, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_kernel_ptr(c->p.ngroups, false,
+                                                                           c->p.thin_approx || !c->hopen.empty()),
+                                                          c->block, smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -323,7 +377,26 @@ arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
     if (seeds_limit > 0 && seeds_limit < A.nseeds) A.nseeds = seeds_limit;
     CK(launch_seed_reset(A, c->qcap, A.nseeds, c->stream));
     CK(record_event(c, c->ev[0]));
+    if (c->p.thin_approx && c->nsrc_dev > 0) {
+        // Sec. 2.6: rays start at each source's radius; the cells inside it
+        // take the thin-limit absorption
+        CK(launch_thin_begin(c->seeds, A.nseeds, c->rthin, c->rnext, c->nsrc_dev, c->stream));
+        ThinFillArgs T;
+        T.n = c->n;
+        T.nb = c->nb;
+        T.nsrc = c->nsrc_dev;
+        T.src = c->dsrc;
+        T.rthin = c->rthin;
+        T.nbase = (float)(12 << (2 * c->p.l_base));
+        T.rec = c->rec;
+        T.thin = &c->scal->thin;
+        T.rounding = &c->scal->rounding;
+        CK(launch_thin_fill(T, c->stream));
+    }
     if (A.nseeds > 0) CK(launch_trace(A, trace_grid(c), c->block, c->stream));
+    // the autotuner's partial traces (seeds_limit) leave the radii as they are
+    if (c->p.thin_approx && c->nsrc_dev > 0 && seeds_limit == 0)
+        CK(launch_thin_commit(c->rthin, c->rnext, c->nsrc_dev, c->stream));
     CK(record_event(c, c->ev[1]));
     FinalizeArgs F;
     memset(&F, 0, sizeof F);
@@ -348,8 +421,8 @@ arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
     F.heat = c->heat;
     F.absorbed_part = c->absorbed_part;
     CK(launch_finalize(F, c->nparts, c->stream));
-    CK(launch_budget(c->absorbed_part, c->nparts, &c->scal->escaped, &c->scal->rounding, c->scal->budget_out,
-                     c->stream));
+    CK(launch_budget(c->absorbed_part, c->nparts, &c->scal->escaped, &c->scal->rounding, &c->scal->thin,
+                     c->scal->budget_out, c->stream));
     return ARC_OK;
 }
 
@@ -441,9 +514,10 @@ arc_status arc_create(arc_ctx** out, const arc_grid* g, const arc_params* p, voi
     // allow the largest tuning (256 threads x 256 deque entries) once, for every context
     for (int ng : {1, 3, 4})
         for (bool rec : {false, true})
-            if (cudaFuncSetAttribute(trace_kernel_ptr(ng, rec), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     trace_smem_bytes(256, 8)) != cudaSuccess)
-                return bail(ARC_E_CUDA);
+            for (bool ext : {false, true})
+                if (cudaFuncSetAttribute(trace_kernel_ptr(ng, rec, ext), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         trace_smem_bytes(256, 8)) != cudaSuccess)
+                    return bail(ARC_E_CUDA);
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(ARC_E_CUDA);
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return bail(ARC_E_CUDA);
@@ -518,6 +592,7 @@ arc_status arc_add_sources(arc_ctx* c, int nsrc, const double* pos, const double
         s.id = (uint32_t)c->hsrc.size();
         c->hsrc.push_back(s);
     }
+    c->hopen.clear();   // a mask covers the sources it was set for
     c->src_dirty = true;
     c->graph_valid = false;
     return ARC_OK;
@@ -526,6 +601,7 @@ arc_status arc_add_sources(arc_ctx* c, int nsrc, const double* pos, const double
 arc_status arc_clear_sources(arc_ctx* c) {
     if (!c) return ARC_E_INVALID;
     c->hsrc.clear();
+    c->hopen.clear();
     c->src_dirty = true;
     c->graph_valid = false;
     return ARC_OK;
@@ -540,6 +616,7 @@ arc_status arc_trace(arc_ctx* c, double dt, float** gamma, float** heat, double*
     st = enqueue_trace(c);
     if (st != ARC_OK) return st;
     c->traced = true;
+    c->last_dt = dt;
     if (gamma) *gamma = c->gamma;
     if (heat) *heat = c->heat;
     if (budget) {
@@ -833,6 +910,62 @@ arc_status arc_autotune(arc_ctx* c, int max_sources, int reps, double* best_ms) 
 
 const char* arc_last_error(const arc_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+arc_status arc_set_emission_mask(arc_ctx* c, const uint8_t* open, int64_t count) {
+    if (!c) return ARC_E_INVALID;
+    if (!open || count == 0) {
+        if (!c->hopen.empty()) c->graph_valid = false;
+        c->hopen.clear();
+        c->src_dirty = true;
+        return ARC_OK;
+    }
+    if (c->p.thin_approx) return fail(c, ARC_E_INVALID, "emission masks do not combine with thin_approx");
+    const int64_t nbase = 12ll << (2 * c->p.l_base);
+    if (count != (int64_t)c->hsrc.size() * nbase)
+        return fail(c, ARC_E_INVALID, "mask has %lld entries, expected %lld (sources x 12*4^l_base)",
+                    (long long)count, (long long)c->hsrc.size() * nbase);
+    c->hopen.assign(open, open + count);
+    c->src_dirty = true;
+    c->graph_valid = false;
+    return ARC_OK;
+}
+
+arc_status arc_set_thin_radii(arc_ctx* c, const double* radii, int nsrc) {
+    if (!c) return ARC_E_INVALID;
+    if (!c->p.thin_approx) return fail(c, ARC_E_STATE, "thin_approx is off");
+    if (!radii || nsrc != (int)c->hsrc.size())
+        return fail(c, ARC_E_INVALID, "need one radius per source (%d)", (int)c->hsrc.size());
+    for (int i = 0; i < nsrc; ++i)
+        if (!(radii[i] >= 0.0) || !isfinite(radii[i])) return fail(c, ARC_E_INVALID, "radius %d invalid", i);
+    arc_status st = upload_sources(c);
+    if (st != ARC_OK) return st;
+    if (c->nsrc_dev == 0) return ARC_OK;
+    std::vector<float> h(c->nsrc_dev);
+    for (int i = 0; i < c->nsrc_dev; ++i) h[i] = (float)radii[c->dev_ids[i]];
+    CK(cudaMemcpyAsync(c->rthin, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ARC_OK;
+}
+
+arc_status arc_get_thin_radii(arc_ctx* c, double* radii, int nsrc, double* thin_photons) {
+    if (!c) return ARC_E_INVALID;
+    if (!c->p.thin_approx) return fail(c, ARC_E_STATE, "thin_approx is off");
+    if (radii && nsrc != (int)c->hsrc.size())
+        return fail(c, ARC_E_INVALID, "need room for one radius per source (%d)", (int)c->hsrc.size());
+    std::vector<float> h(c->nsrc_dev);
+    double thin = 0.0;
+    if (c->nsrc_dev > 0 && !c->src_dirty)
+        CK(cudaMemcpyAsync(h.data(), c->rthin, h.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&thin, &c->scal->thin, sizeof thin, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (radii) {
+        for (int i = 0; i < nsrc; ++i) radii[i] = 0.0;
+        if (!c->src_dirty)
+            for (int i = 0; i < c->nsrc_dev; ++i) radii[c->dev_ids[i]] = (double)h[i];
+    }
+    if (thin_photons) *thin_photons = c->traced ? thin * PHOT_UNIT * c->last_dt : 0.0;
+    return ARC_OK;
+}
+
 void arc_destroy(arc_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -841,7 +974,8 @@ void arc_destroy(arc_ctx* c) {
     for (int i = 0; i < 4; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     void* ptrs[] = {c->nH, c->xHI, c->xHeI, c->xHeII, c->T, c->rec, c->gamma, c->heat,
-                    c->dsrc, c->seeds, c->qdata, c->qseq, c->scal, c->absorbed_part, c->mlp, c->fb_list};
+                    c->dsrc, c->seeds, c->qdata, c->qseq, c->scal, c->absorbed_part, c->mlp, c->fb_list,
+                    c->rthin, c->rnext, c->dopen};
     for (void* q : ptrs) dfree(q);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -76,7 +76,9 @@ struct __align__(16) SourceDev {
     float4 pos_thr;   // x, y, z [cells], photon threshold of one l_base ray [PHOT_UNIT]
     float4 N0;        // photons of one l_base ray per group [PHOT_UNIT]
     uint32_t id;      // index in the order the caller added the sources
-    uint32_t pad[3];
+    float cthr0;      // group-0 photons of one l_base ray after optical depth 0.1
+                      // (N0.x exp(-0.1)), the optically thin radius test (Sec. 2.6)
+    uint32_t pad[2];
 };
 
 // Arguments of the tracer kernels.
@@ -92,6 +94,15 @@ struct TraceArgs {
     float rsplit[ARC_MAX_LEVEL + 1];   // split distance per level [cells]
     float pixw[ARC_MAX_LEVEL + 1];     // pixel width per unit distance, sqrt(Omega_l)
     int geo_corr;                      // geometric correction (Sec. 2.5) on
+    // anisotropic escape (Sec. 2.2): open[src * nbase + pix] == 0 blocks emitted
+    // ray pix of device source src (nullptr: all open)
+    const uint8_t* open;
+    int nbase;                         // rays emitted per source, 12 * 4^l_base
+    // optically thin approximation (Sec. 2.6, extended kernels only): per
+    // device source, the minimum over its rays of the length while the group-0
+    // optical depth is below 0.1, as float bits (atomicMin)
+    float* rnext;
+    double* thin;                      // photons deposited by the thin fill [PHOT_UNIT]
     // emitted work: static array consumed by ticket
     const Entry* seeds;
     int nseeds;
@@ -245,16 +256,36 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding, double* out,
+cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding,
+                          const double* thin, double* out,
                           cudaStream_t s);
 cudaError_t launch_validate(const float* nH, const float* xHI, const float* xHeI,
                             const float* xHeII, const float* T, long long ncell,
                             unsigned int* status, cudaStream_t s);
+// Optically thin approximation (Sec. 2.6): seeds start at rthin of their
+// source and rnext is reset (begin); cells within rthin of a source take the
+// thin-limit absorption (fill); rthin takes the radii the trace measured
+// (commit).  All arrays are per device source.
+struct ThinFillArgs {
+    int n, nb, nsrc;
+    const SourceDev* src;
+    const float* rthin;
+    float nbase;              // rays per source: S_b = N0_b * nbase
+    float4* rec;
+    double* thin;             // ledger of the fill's photons [PHOT_UNIT]
+    double* rounding;         // rounding ledger of the FP32 cell sums
+};
+cudaError_t launch_thin_begin(Entry* seeds, int nseeds, const float* rthin, float* rnext, int nsrc,
+                              cudaStream_t s);
+cudaError_t launch_thin_fill(const ThinFillArgs& a, cudaStream_t s);
+cudaError_t launch_thin_commit(float* rthin, const float* rnext, int nsrc, cudaStream_t s);
 cudaError_t launch_make_seeds(const SourceDev* src, int nsrc, int l_base, Entry* seeds,
                               cudaStream_t s);
 cudaError_t launch_chem(const ChemArgs& a, cudaStream_t s);
 cudaError_t launch_rt_timestep(const ChemArgs& c, float sigd, float eps, unsigned* out, cudaStream_t s);
 int trace_smem_bytes(int block, int stack_log2);
-const void* trace_kernel_ptr(int ng, bool rec = false);   // rec: the per-ray-record variant
+// rec: the per-ray-record variant; ext: the variant with emission masks and
+// the optically thin radius
+const void* trace_kernel_ptr(int ng, bool rec = false, bool ext = false);
 
 }  // namespace arc

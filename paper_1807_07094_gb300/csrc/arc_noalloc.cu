@@ -81,6 +81,7 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     if (!g || !p || !nH || !xHI || !xHeI || !xHeII || !gamma || !heat) return ARC_E_INVALID;
     if (g->n < 1 || g->n > NA_MAX_N || !(g->box_cm > 0)) return ARC_E_INVALID;
     if (nsrc < 0 || nsrc > NA_MAX_SRC || (nsrc > 0 && (!pos || !ndot))) return ARC_E_INVALID;
+    if (p->thin_approx) return ARC_E_INVALID;   // needs per-source state across traces
     if (p->ngroups < 1 || p->ngroups > ARC_MAX_GROUPS || p->l_base < 1 || p->l_base > NA_MAX_LBASE ||
         p->l_max < p->l_base || p->l_max > ARC_MAX_LEVEL || !(p->phi > 0) ||
         !(p->term_frac > 0 && p->term_frac < 1) || !(p->Y >= 0 && p->Y < 1))
@@ -148,7 +149,8 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
                                       (float)(p->term_frac * tot));
         hsrc[k].N0 = make_float4(N0[0], N0[1], N0[2], N0[3]);
         hsrc[k].id = (uint32_t)i;
-        hsrc[k].pad[0] = hsrc[k].pad[1] = hsrc[k].pad[2] = 0;
+        hsrc[k].cthr0 = 0.f;   // no optically thin radius on this path
+        hsrc[k].pad[0] = hsrc[k].pad[1] = 0;
     }
     const int per_src = 3 << (2 * p->l_base);
     const int nseeds = ns * per_src;
@@ -250,7 +252,7 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     F.heat = heat;
     F.absorbed_part = parts;
     NA_CK(launch_finalize(F, NA_NPARTS, s));
-    NA_CK(launch_budget(parts, NA_NPARTS, &scal->escaped, &scal->rounding, scal->budget_out, s));
+    NA_CK(launch_budget(parts, NA_NPARTS, &scal->escaped, &scal->rounding, nullptr, scal->budget_out, s));
 
     // the source table was copied from this stack frame: wait before returning
     NaScalars S;

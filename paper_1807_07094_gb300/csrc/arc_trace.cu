@@ -185,11 +185,63 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t x) {
     return x;
 }
 
-// Centre of nested pixel pix at level (nside = 2^level) as a unit vector.
-// The 12 base faces form three rows of four (north, equator, south); inside a
-// face the pixel's (x, y) come from the even/odd bits of its index, which fix
-// its ring (latitude) and its position along the ring (longitude).
-__device__ float3 healpix_dir(int level, uint64_t pix) {
+// ------------------------------------------------------------ pair arithmetic
+// Unevaluated FP32 pairs hi + lo (~2^-44 relative) for the ray geometry.  The
+// explicit _rn operations keep the compiler from contracting or reordering.
+struct F2 {
+    float h, l;
+};
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float e = __fadd_rn(two_sum_err(a.h, b.h), __fadd_rn(a.l, b.l));
+    return fast_two_sum(s, e);
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2 f2_neg(F2 a) { return F2{-a.h, -a.l}; }
+// num / den for integers exactly representable in FP32
+__device__ __forceinline__ F2 f2_ratio(float num, float den) {
+    const float h = __fdiv_rn(num, den);
+    return F2{h, __fdiv_rn(fmaf(-h, den, num), den)};
+}
+__device__ __forceinline__ F2 f2_sqrt(F2 x) {
+    const float h = __fsqrt_rn(x.h);
+    if (h == 0.0f) return F2{0.0f, 0.0f};
+    const float r = __fadd_rn(fmaf(-h, h, x.h), x.l);   // x - h^2 (the fma part is exact)
+    return fast_two_sum(h, __fdiv_rn(r, __fadd_rn(h, h)));
+}
+
+// sin and cos of pi j / 64, j = -16..16, as pairs (sin h, sin l, cos h, cos l):
+// each block of the tracer fills this table once from FP64 sincospi
+__shared__ float4 s_sincos[33];
+__device__ __forceinline__ void fill_sincos_table() {
+    if (threadIdx.x < 33) {
+        double sd, cd;
+        sincospi((double)((int)threadIdx.x - 16) / 64.0, &sd, &cd);
+        const float sh = (float)sd, ch = (float)cd;
+        s_sincos[threadIdx.x] = make_float4(sh, (float)(sd - (double)sh), ch, (float)(cd - (double)ch));
+    }
+    __syncthreads();
+}
+
+// Centre of nested pixel pix at level (nside = 2^level) as a unit vector of
+// pairs (u[a] = hi + lo, ~1e-13).  The 12 base faces form three rows of four
+// (north, equator, south); inside a face the pixel's (x, y) come from the
+// even/odd bits of its index, which fix its ring (latitude) and its position
+// along the ring (longitude).  Why pairs: a direction off by one FP32 ulp
+// moves the ray ~t 1e-7 cells sideways, which behind optically thick cells
+// (tens of optical depths per cell) changes the transmitted photons by
+// ~1e-4.  Everything is FP32 arithmetic: z from its exact rational form,
+// sin(theta) by a pair square root, and sin/cos of the longitude from the
+// table above plus a short Taylor series in a remainder below pi / 128.
+__device__ void healpix_dir(int level, uint64_t pix, F2 u[3]) {
     const int ns = 1 << level;
     const uint32_t face = (uint32_t)(pix >> (2 * level));
     const uint32_t ipf = (uint32_t)(pix & ((1ull << (2 * level)) - 1ull));
@@ -197,18 +249,21 @@ __device__ float3 healpix_dir(int level, uint64_t pix) {
     const int row = (int)(face >> 2);
     const int ring = (row + 2) * ns - ix - iy - 1;      // 1 .. 4 ns - 1 from the north pole
     int nr, shift;
-    float z, sth;
-    if (ring < ns || ring > 3 * ns) {                   // polar caps: z = +-(1 - nr^2 / (3 ns^2))
+    F2 z, sth;
+    if (ring < ns || ring > 3 * ns) {                   // polar caps: z = +-(1 - a), a = nr^2 / (3 ns^2)
         nr = ring < ns ? ring : 4 * ns - ring;
-        const float f = (float)nr / (float)ns;
-        const float a = f * f * (1.0f / 3.0f);
-        z = ring < ns ? 1.0f - a : a - 1.0f;
-        sth = sqrtf(a * (2.0f - a));
+        const float f = __fdiv_rn((float)nr, (float)ns);   // exact (ns is a power of two)
+        const F2 f2 = fast_two_sum(__fmul_rn(f, f), fmaf(f, f, -__fmul_rn(f, f)));
+        const float ah = __fdiv_rn(f2.h, 3.0f);
+        const F2 a = fast_two_sum(ah, __fdiv_rn(__fadd_rn(fmaf(-ah, 3.0f, f2.h), f2.l), 3.0f));
+        const F2 one_minus = f2_add(F2{1.0f, 0.0f}, f2_neg(a));
+        z = ring < ns ? one_minus : f2_neg(one_minus);
+        sth = f2_sqrt(f2_mul(a, f2_add(F2{2.0f, 0.0f}, f2_neg(a))));   // a (2 - a)
         shift = 0;
-    } else {                                            // belt: z linear in the ring index
+    } else {                                            // belt: z = 2 (2 ns - ring) / (3 ns)
         nr = ns;
-        z = (float)(2 * ns - ring) * (2.0f / 3.0f) / (float)ns;
-        sth = sqrtf((1.0f - z) * (1.0f + z));
+        z = f2_ratio((float)(2 * (2 * ns - ring)), (float)(3 * ns));
+        sth = f2_sqrt(f2_add(F2{1.0f, 0.0f}, f2_neg(f2_mul(z, z))));   // 1 - z^2
         shift = (ring - ns) & 1;
     }
     const int lon = 2 * (int)(face & 3u) + (row == 1 ? 0 : 1);
@@ -216,24 +271,58 @@ __device__ float3 healpix_dir(int level, uint64_t pix) {
     if (jp > 4 * ns) jp -= 4 * ns;
     if (jp < 1) jp += 4 * ns;
     // longitude / pi = m / (4 nr), reduced exactly (in integers) to the
-    // nearest multiple of 1/2 plus a small offset, so that a component that
-    // is nearly zero keeps its relative accuracy: its absolute error would
-    // otherwise become a large relative error in 1/u, and the crossing of a
-    // plane the ray runs almost parallel to would move by ~1e-3 cells
+    // nearest multiple of 1/2 (k) plus q = mq / (4 nr), |q| <= 1/4, and q to
+    // the nearest multiple of 1/64 (j) plus d = dn / (64 nr), |d| <= 1/128
     const int m = 2 * jp - shift - 1;
     const int half = 2 * nr;
-    const int k = (m + nr) / half;                      // nearest multiple of 1/2 (m >= 0)
-    const float qr = (float)(m - k * half) / (float)(4 * nr);   // |qr| <= 1/4
-    float s0, c0;
-    sincospif(qr, &s0, &c0);
-    float sp, cp;
+    const int k = (m + nr) / half;                      // m >= 0
+    const int mq = m - k * half;                        // -nr .. nr
+    const int j = (int)rintf(__fdiv_rn((float)(16 * mq), (float)nr));
+    const F2 d = f2_ratio((float)(16 * mq - j * nr), (float)(64 * nr));
+    const F2 th = f2_mul(d, F2{3.14159274101257324f, -8.74227766e-8f});   // pi d
+    const float t2 = __fmul_rn(th.h, th.h);
+    // sin(th) = th - th^3/6 + th^5/120, cos(th) = 1 - th^2/2 + th^4/24 - th^6/720
+    // (|th| < 0.025: the next terms are below 2e-15)
+    const F2 sb = fast_two_sum(th.h, __fadd_rn(th.l, __fmul_rn(__fmul_rn(th.h, t2),
+                                                               fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f))));
+    const float t2l = fmaf(th.h, th.h, -t2) + 2.0f * th.h * th.l;   // th^2 = t2 + t2l
+    const F2 c0 = fast_two_sum(1.0f, -0.5f * t2);
+    const F2 cb = fast_two_sum(c0.h, __fadd_rn(c0.l, fmaf(-0.5f, t2l,
+                                                          __fmul_rn(__fmul_rn(t2, t2),
+                                                                    fmaf(t2, -1.0f / 720.0f, 1.0f / 24.0f)))));
+    const float4 tab = s_sincos[j + 16];
+    const F2 sa{tab.x, tab.y}, ca{tab.z, tab.w};
+    const F2 s0 = f2_add(f2_mul(sa, cb), f2_mul(ca, sb));            // sin(pi q)
+    const F2 c0q = f2_add(f2_mul(ca, cb), f2_neg(f2_mul(sa, sb)));   // cos(pi q)
+    F2 sp, cp;
     switch (k & 3) {
-        case 0: sp = s0; cp = c0; break;
-        case 1: sp = c0; cp = -s0; break;
-        case 2: sp = -s0; cp = -c0; break;
-        default: sp = -c0; cp = s0; break;
+        case 0: sp = s0; cp = c0q; break;
+        case 1: sp = c0q; cp = f2_neg(s0); break;
+        case 2: sp = f2_neg(s0); cp = f2_neg(c0q); break;
+        default: sp = f2_neg(c0q); cp = s0; break;
     }
-    return make_float3(sth * cp, sth * sp, z);
+    u[0] = f2_mul(sth, cp);
+    u[1] = f2_mul(sth, sp);
+    u[2] = z;
+}
+
+// 1/u as a pair ih + il: ih the FP32 reciprocal of the high part, il from the
+// residual 1 - (uh + ul) ih.  A zero component gives ih = +-inf, il = 0.
+__device__ __forceinline__ void inv_pair(F2 u, float& ih, float& il) {
+    ih = __frcp_rn(u.h);
+    il = (u.h == 0.0f) ? 0.0f : __fmul_rn(fmaf(-u.l, ih, fmaf(-u.h, ih, 1.0f)), ih);
+}
+
+// floor(o + r u) for the start cell, with u a pair: the sum is formed as a
+// pair and the floor taken of its exact value
+__device__ __forceinline__ int start_cell(float o, float r, F2 u) {
+    const F2 p = f2_mul(F2{r, 0.0f}, u);
+    const float sh = __fadd_rn(o, p.h);
+    const float low = __fadd_rn(two_sum_err(o, p.h), p.l);
+    float c = floorf(sh);
+    if (sh == c && low < 0.0f) c -= 1.0f;
+    else if (low > 0.0f && low >= __fsub_rn(c + 1.0f, sh)) c += 1.0f;
+    return (int)c;
 }
 
 // ------------------------------------------------------------------ work queue
@@ -338,14 +427,20 @@ __device__ int q_pop_warp(const TraceArgs& A, Entry& e, int want, int lane) {
 }
 
 // ------------------------------------------------------------------ ray state
-enum : int { EV_NONE = 0, EV_SPLIT = 1, EV_ESC = 2, EV_TERM = 3 };
+// EV_BLOCK: an emitted ray whose direction the source's mask blocks (Sec. 2.2)
+enum : int { EV_NONE = 0, EV_SPLIT = 1, EV_ESC = 2, EV_TERM = 3, EV_BLOCK = 4 };
 
+// Distances along the ray are unevaluated FP32 pairs (hi + lo, ~2^-44
+// relative): with plain FP32 a crossing distance t is off by ~t 2^-24 cells,
+// and behind cells of tens of optical depths that moves ~1e-4 of the photons.
 struct Ray {
     float ox, oy, oz;      // source position [cells]
-    float ix, iy, iz;      // 1/u per axis (+-inf for u = 0)
-    float tx, ty, tz;      // distance to the next plane per axis
-    int cx, cy, cz;        // current cell
-    float r, rstop, thr;
+    float ix, iy, iz;      // 1/u per axis (+-inf for u = 0), high parts
+    float ilx, ily, ilz;   // low parts of 1/u
+    int cx, cy, cz;        // current cell (the distances to its faces are
+                           // recomputed each segment rather than carried)
+    float r, rl;           // distance travelled (hi + lo)
+    float rstop, thr;
     float4 N;              // photons per group (high part)
     float4 Nl;             // low part: the photons are N + Nl
     float4 kap;            // optical depth per cell length of the current cell
@@ -354,20 +449,38 @@ struct Ray {
     uint32_t src;
     int level;
     uint32_t visits;
+    float cthr;            // thin radius: group-0 photons at optical depth 0.1 of this
+                           // ray's share; 0 once reached (or the group is empty)
 };
 
-__device__ __forceinline__ float next_plane_t(int c, float o, float inv) {
-    // u > 0 (inv > 0): plane c + 1;  u < 0: plane c
-    return ((float)(c + (inv > 0.0f ? 1 : 0)) - o) * inv;
+// distance to the next plane on one axis as a pair th + tl:
+// (P - o)(ih + il) with P - o = ah + al exactly (TwoSum) and the product's
+// rounding error recovered by FMA.  u > 0 (ih > 0): plane c + 1; u < 0: plane
+// c; u = 0 (ih infinite): +inf
+__device__ __forceinline__ float next_plane_t(int c, float o, float ih, float il, float& tl) {
+    const float P = (float)(c + (ih > 0.0f ? 1 : 0));
+    const float ah = __fsub_rn(P, o);
+    const float al = two_sum_err(P, -o);
+    const float th = __fmul_rn(ah, ih);
+    tl = fmaf(al, ih, fmaf(ah, il, fmaf(ah, ih, -th)));
+    const bool par = fabsf(ih) == INFINITY;
+    if (par) tl = 0.0f;
+    return par ? INFINITY : th;
 }
 
 // Start child k of entry e in this lane.  Returns EV_ESC if the child starts
 // outside the box (it then carries its photons straight to the escape ledger).
+// The EXT variant (emission masks, Sec. 2.2; optically thin radius, Sec. 2.6)
+// also returns EV_BLOCK for an emitted ray the source's mask blocks, and
+// EV_SPLIT for a ray that starts at or beyond its split distance (rays
+// launched at the thin radius): it splits at once without tracing a cell.
+template <bool EXT>
 __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int k, Ray& R) {
     R.level = key_level(e.key);
     R.pix = key_pixbase(e.key) + (uint64_t)k;
     R.src = e.src;
     R.r = e.r;
+    R.rl = 0.0f;
     R.N = e.N;
     R.Nl = make_float4(0.f, 0.f, 0.f, 0.f);
     R.visits = 0;
@@ -378,18 +491,25 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
     R.oz = pt.z;
     R.thr = ldexpf(pt.w, -2 * (R.level - A.l_base));
     R.rstop = (R.level < A.l_max) ? A.rsplit[R.level] : INFINITY;
-    const float3 u = healpix_dir(R.level, R.pix);
-    R.ix = 1.0f / u.x;   // +-inf when the component is zero
-    R.iy = 1.0f / u.y;
-    R.iz = 1.0f / u.z;
-    R.cx = (int)floorf(fmaf(R.r, u.x, R.ox));
-    R.cy = (int)floorf(fmaf(R.r, u.y, R.oy));
-    R.cz = (int)floorf(fmaf(R.r, u.z, R.oz));
+    if (EXT) {
+        const float c = ldexpf(__ldg(&S->cthr0), -2 * (R.level - A.l_base));
+        R.cthr = (A.rnext != nullptr && R.N.x > c) ? c : 0.0f;
+        if (A.open != nullptr && R.level == A.l_base && A.open[(size_t)R.src * A.nbase + R.pix] == 0) {
+            R.cthr = 0.0f;
+            return EV_BLOCK;
+        }
+    }
+    F2 u[3];
+    healpix_dir(R.level, R.pix, u);
+    inv_pair(u[0], R.ix, R.ilx);
+    inv_pair(u[1], R.iy, R.ily);
+    inv_pair(u[2], R.iz, R.ilz);
+    R.cx = start_cell(R.ox, R.r, u[0]);
+    R.cy = start_cell(R.oy, R.r, u[1]);
+    R.cz = start_cell(R.oz, R.r, u[2]);
     const int n = A.n;
     if (R.cx < 0 || R.cx >= n || R.cy < 0 || R.cy >= n || R.cz < 0 || R.cz >= n) return EV_ESC;
-    R.tx = (u.x != 0.0f) ? next_plane_t(R.cx, R.ox, R.ix) : INFINITY;
-    R.ty = (u.y != 0.0f) ? next_plane_t(R.cy, R.oy, R.iy) : INFINITY;
-    R.tz = (u.z != 0.0f) ? next_plane_t(R.cz, R.oz, R.iz) : INFINITY;
+    if (EXT && R.r >= R.rstop) return EV_SPLIT;
     R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
     R.kap = ldg_f4(&A.kappa[2 * R.idx]);
     return EV_NONE;
@@ -399,12 +519,22 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
 // distance, Eq. (ion) absorption in each of the NG groups, then step.  The
 // next cell's record is loaded before the current cell's deposit is issued, so
 // the load and the atomic round trip overlap.
-template <int NG, bool REC>
+template <int NG, bool REC, bool EXT>
 __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) {
-    const float t = fminf(R.tx, fminf(R.ty, R.tz));
-    const bool split = R.rstop <= t;
+    // nearest plane; ties go to the lowest axis (x, y, z), as in the step below
+    float tlx, tly, tlz;
+    const float tx = next_plane_t(R.cx, R.ox, R.ix, R.ilx, tlx);
+    const float ty = next_plane_t(R.cy, R.oy, R.iy, R.ily, tly);
+    const float tz = next_plane_t(R.cz, R.oz, R.iz, R.ilz, tlz);
+    const bool ax = tx <= ty && tx <= tz;
+    const bool ay = !ax && ty <= tz;
+    const float t = ax ? tx : (ay ? ty : tz);
+    const float tl = ax ? tlx : (ay ? tly : tlz);
+    // split where r_split <= t exactly (r_split is an FP32 value, t = hi + lo)
+    const bool split = R.rstop < t || (R.rstop == t && tl >= 0.0f);
     const float r1 = split ? R.rstop : t;
-    const float ds = fmaxf(r1 - R.r, 0.0f);
+    const float r1l = split ? 0.0f : tl;
+    const float ds = fmaxf(__fadd_rn(__fsub_rn(r1, R.r), __fsub_rn(r1l, R.rl)), 0.0f);
     const uint64_t idx = R.idx;
     const float4 kap = R.kap;
     const float4 Nh0 = R.N, Nl0 = R.Nl;
@@ -413,6 +543,14 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
     if (NG > 1) absorb(R.N.y, R.Nl.y, kap.y * ds, D.y, E.y);
     if (NG > 2) absorb(R.N.z, R.Nl.z, kap.z * ds, D.z, E.z);
     if (NG > 3) absorb(R.N.w, R.Nl.w, kap.w * ds, D.w, E.w);
+    if (EXT && R.cthr > 0.0f && R.N.x <= R.cthr) {
+        // Sec. 2.6: the group-0 optical depth from the ray's start reaches 0.1
+        // inside this segment, at r + ln(N_in / N_0.1) / kappa_0
+        float ts = r1;
+        if (kap.x > 0.0f) ts = fminf(fmaxf(R.r + logf(Nh0.x / R.cthr) / kap.x, R.r), r1);
+        atomicMin(reinterpret_cast<int*>(A.rnext) + R.src, __float_as_int(ts));
+        R.cthr = 0.0f;
+    }
     float sumN = R.N.x;
     if (NG > 1) sumN += R.N.y;
     if (NG > 2) sumN += R.N.z;
@@ -466,23 +604,21 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
         }
     }
     R.r = r1;
+    R.rl = r1l;
     int ev = term ? EV_TERM : (split ? EV_SPLIT : EV_NONE);
     if (ev == EV_NONE) {
         // step across the nearest face; ties go to the lowest axis (x, y, z)
         const int n = A.n;
         bool out;
-        if (R.tx <= R.ty && R.tx <= R.tz) {
+        if (ax) {
             R.cx += (R.ix > 0.f) ? 1 : -1;
             out = R.cx < 0 || R.cx >= n;
-            if (!out) R.tx = next_plane_t(R.cx, R.ox, R.ix);
-        } else if (R.ty <= R.tz) {
+        } else if (ay) {
             R.cy += (R.iy > 0.f) ? 1 : -1;
             out = R.cy < 0 || R.cy >= n;
-            if (!out) R.ty = next_plane_t(R.cy, R.oy, R.iy);
         } else {
             R.cz += (R.iz > 0.f) ? 1 : -1;
             out = R.cz < 0 || R.cz >= n;
-            if (!out) R.tz = next_plane_t(R.cz, R.oz, R.iz);
         }
         if (out) {
             ev = EV_ESC;
@@ -526,7 +662,7 @@ constexpr int HEARTBEAT_EVERY = 1024; // event rounds between progress signals
                                  // (3: 80 registers, 24 warps/SM; measured 16 % faster than 2
                                  // blocks without spills, and faster than 4)
 #endif
-template <int NG, bool REC>
+template <int NG, bool REC, bool EXT>
 __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -543,7 +679,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
     __shared__ WarpTally tally_all[8];
     WarpTally& W = tally_all[wib];
     if (lane == 0) W = WarpTally{};
-    __syncwarp();
+    fill_sincos_table();   // also orders the tallies' initialisation
     unsigned nseg = 0;                 // per lane
     double rounding = 0.0;             // photons the FP32 cell sums rounded away (exact)
     unsigned round = 0;
@@ -663,21 +799,28 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                 }
                 top += (unsigned)got;
             }
-            // hand the children of the newest items to idle lanes (depth first)
+            // hand the children of the newest items to idle lanes (depth first):
+            // each lane notes its item's slot and child, and all lanes that took
+            // one start their rays together after the loop (a ray start is a
+            // few hundred instructions: started item by item, only the 1-4
+            // lanes of that item would be active).  Slots given up here are not
+            // reused before the event phase, so the items are still in place.
+            int take_slot = -1, take_k = 0;
             while (idle != 0 && top != bot) {
-                const Entry e = stack[(top - 1) & cmask];
-                const int k0 = key_k(e.key);
+                const unsigned slot = (top - 1) & cmask;
+                const uint64_t key = stack[slot].key;
+                const int k0 = key_k(key);
                 const int avail = 4 - k0;
                 const int rank = __popc(idle & lt_mask);
                 const bool mine = ((idle >> lane) & 1u) && rank < avail;
                 const unsigned taken = __ballot_sync(FULL, mine);
                 if (mine) {
-                    ev = start_ray(A, e, k0 + rank, R);
-                    active = true;
+                    take_slot = (int)slot;
+                    take_k = k0 + rank;
                 }
                 if (lane == 0) {
                     W.nrays += (unsigned)__popc(taken);
-                    W.maxlev = max(W.maxlev, (unsigned)key_level(e.key));
+                    W.maxlev = max(W.maxlev, (unsigned)key_level(key));
                 }
                 idle &= ~taken;
                 __syncwarp();
@@ -685,9 +828,13 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                 if (ntake >= avail) {
                     top -= 1;
                 } else if (lane == 0) {
-                    stack[(top - 1) & cmask].key = make_key(key_pixbase(e.key), key_level(e.key), k0 + ntake);
+                    stack[slot].key = make_key(key_pixbase(key), key_level(key), k0 + ntake);
                 }
                 __syncwarp();
+            }
+            if (take_slot >= 0) {
+                ev = start_ray<EXT>(A, stack[take_slot], take_k, R);
+                active = true;
             }
         }
 
@@ -696,7 +843,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
             float rerr = 0.0f;   // rounding ledger of this batch (a few ulps of its deposits)
 #pragma unroll 1
             for (int it = 0; it < SEG_BATCH; ++it) {
-                ev = segment<NG, REC>(A, R, rerr);
+                ev = segment<NG, REC, EXT>(A, R, rerr);
                 nseg++;
                 if (ev != EV_NONE) break;
             }
@@ -730,6 +877,10 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                 }
             }
             const bool is_split = has_ev && ev == EV_SPLIT;
+            // Sec. 2.6: a ray that ends (escape, threshold) before its group-0
+            // optical depth reaches 0.1 offers its whole length
+            if (EXT && has_ev && !is_split && R.cthr > 0.0f)
+                atomicMin(reinterpret_cast<int*>(A.rnext) + R.src, __float_as_int(R.r));
             if (has_ev && !is_split) {
                 if (ev == EV_ESC) {
                     atomicAdd(&W.esc, ((double)R.N.x + (double)R.Nl.x) + ((double)R.N.y + (double)R.Nl.y) +
@@ -774,7 +925,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                     // also inherits the parent's sub-ulp low part, so no photon
                     // is lost and no cell receives a spurious deposit
                     const float4 keep = R.Nl;
-                    ev = start_ray(A, e, 0, R);
+                    ev = start_ray<EXT>(A, e, 0, R);
                     fold_low(R.N.x, R.Nl.x, keep.x);
                     fold_low(R.N.y, R.Nl.y, keep.y);
                     fold_low(R.N.z, R.Nl.z, keep.z);
@@ -905,6 +1056,7 @@ __global__ void k_reset(TraceArgs A, unsigned long long qcap, int nseeds) {
         *A.heartbeat = 0;
         *A.escaped = 0.0;
         *A.rounding = 0.0;
+        if (A.thin) *A.thin = 0.0;
         for (int i = 0; i < CNT_N; ++i) A.counters[i] = 0;
         A.counters[CNT_TRACES_TOTAL] += 1;
         if (A.nrec) *A.nrec = 0;
@@ -965,7 +1117,7 @@ __global__ void k_finalize(const FinalizeArgs F) {
 }
 
 __global__ void k_budget(const double* part, int nparts, const double* escaped, const double* rounding,
-                         double* out) {
+                         const double* thin, double* out) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
@@ -975,8 +1127,89 @@ __global__ void k_budget(const double* part, int nparts, const double* escaped, 
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        out[0] = t + *rounding;   // the cell sums plus what their FP32 additions rounded away
+        // the cell sums plus what their FP32 additions rounded away, less the
+        // thin fill's photons, which no ray carried (Sec. 2.6)
+        out[0] = t + *rounding - (thin ? *thin : 0.0);
         out[1] = *escaped;
+    }
+}
+
+// ------------------------------------------------------------------ thin region
+// Sec. 2.6.  begin: the emitted rays of each source start at its radius R, and
+// the radius candidates are reset to +inf.
+__global__ void k_thin_begin(Entry* seeds, int nseeds, const float* rthin, float* rnext, int nsrc) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nseeds; q += stride)
+        seeds[q].r = rthin[seeds[q].src];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsrc; s += stride) rnext[s] = INFINITY;
+}
+
+// Cells whose centre lies within R of a source absorb, per group, the thin
+// limit of Eq. (ion) summed over the rays crossing them: S_b kappa_b V /
+// (4 pi r^2) (kappa_b per cell length, r in cells from the source to the
+// centre, floored at half a cell where 1/r^2 diverges).  The photons go through
+// the same returning atomics and rounding ledger as the rays' deposits and are
+// counted in the thin ledger, so that the budget still closes over the rays.
+// Grid: x strides over the cube of cells around one source, y over sources.
+__global__ void k_thin_fill(const ThinFillArgs F) {
+    constexpr float INV_4PI = 0.0795774715459476679f;
+    double got = 0.0, err = 0.0;
+    for (int s = blockIdx.y; s < F.nsrc; s += gridDim.y) {
+        const float R = F.rthin[s];
+        if (!(R > 0.0f)) continue;
+        const float4 pt = F.src[s].pos_thr;
+        const float4 N0 = F.src[s].N0;
+        const float4 S = make_float4(N0.x * F.nbase, N0.y * F.nbase, N0.z * F.nbase, N0.w * F.nbase);
+        // cells with centre c + 1/2 in [o - R, o + R] per axis, clipped to the
+        // box (the extent is capped at 2n so that the bounds stay integers)
+        const float o[3] = {pt.x, pt.y, pt.z};
+        const float Rb = fminf(R, 2.0f * (float)F.n);
+        int lo[3], m[3];
+        bool empty = false;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = max(0, (int)ceilf(o[a] - Rb - 0.5f));
+            const int hi = min(F.n - 1, (int)floorf(o[a] + Rb - 0.5f));
+            m[a] = hi - lo[a] + 1;
+            empty |= m[a] <= 0;
+        }
+        if (empty) continue;
+        const long long myz = (long long)m[1] * m[2];
+        const long long tot = (long long)m[0] * myz;
+        const float R2 = R * R;
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+             q += (long long)gridDim.x * blockDim.x) {
+            const int i = lo[0] + (int)(q / myz);
+            const long long rem = q % myz;
+            const int j = lo[1] + (int)(rem / m[2]);
+            const int k = lo[2] + (int)(rem % m[2]);
+            const float dx = (float)i + 0.5f - o[0], dy = (float)j + 0.5f - o[1], dz = (float)k + 0.5f - o[2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!(r2 < R2)) continue;
+            const float f = INV_4PI / fmaxf(r2, 0.25f);
+            const uint64_t idx = brick_index(i, j, k, F.nb);
+            const float4 kap = F.rec[2 * idx];
+            const float4 D = make_float4(S.x * kap.x * f, S.y * kap.y * f, S.z * kap.z * f, S.w * kap.w * f);
+            if (D.x == 0.f && D.y == 0.f && D.z == 0.f && D.w == 0.f) continue;
+            err += (double)deposit<4>(F.rec, idx, D, make_float4(0.f, 0.f, 0.f, 0.f));
+            got += ((double)D.x + (double)D.y) + ((double)D.z + (double)D.w);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        got += __shfl_down_sync(FULL, got, o);
+        err += __shfl_down_sync(FULL, err, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (got != 0.0) atomicAdd(F.thin, got);
+        if (err != 0.0) atomicAdd(F.rounding, err);
+    }
+}
+
+// commit: the radius each source measured becomes the one of the next trace
+// (0 when no ray of the source offered one)
+__global__ void k_thin_commit(float* rthin, const float* rnext, int nsrc) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsrc; s += gridDim.x * blockDim.x) {
+        const float v = rnext[s];
+        rthin[s] = (v < INFINITY) ? v : 0.0f;
     }
 }
 
@@ -986,16 +1219,18 @@ __global__ void k_budget(const double* part, int nparts, const double* escaped, 
 int trace_smem_bytes(int block, int stack_log2) {
     return (block / 32) * (1 << stack_log2) * (int)sizeof(Entry);
 }
-// the tracer is specialised on the number of frequency groups carried
-const void* trace_kernel_ptr(int ng, bool rec) {
-    if (rec) {
-        if (ng <= 1) return (const void*)k_trace<1, true>;
-        if (ng <= 3) return (const void*)k_trace<3, true>;
-        return (const void*)k_trace<4, true>;
-    }
-    if (ng <= 1) return (const void*)k_trace<1, false>;
-    if (ng <= 3) return (const void*)k_trace<3, false>;
-    return (const void*)k_trace<4, false>;
+// the tracer is specialised on the number of frequency groups carried, on the
+// per-ray records (test aid) and on the extended emission (masks, Sec. 2.2;
+// optically thin radius, Sec. 2.6)
+template <bool REC, bool EXT>
+const void* trace_kernel_ng(int ng) {
+    if (ng <= 1) return (const void*)k_trace<1, REC, EXT>;
+    if (ng <= 3) return (const void*)k_trace<3, REC, EXT>;
+    return (const void*)k_trace<4, REC, EXT>;
+}
+const void* trace_kernel_ptr(int ng, bool rec, bool ext) {
+    if (rec) return ext ? trace_kernel_ng<true, true>(ng) : trace_kernel_ng<true, false>(ng);
+    return ext ? trace_kernel_ng<false, true>(ng) : trace_kernel_ng<false, false>(ng);
 }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
@@ -1022,26 +1257,50 @@ cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int n
     k_reset<<<152 * 2, 256, 0, s>>>(a, qcap, nseeds);
     return cudaGetLastError();
 }
+template <bool REC, bool EXT>
+void launch_trace_ng(const TraceArgs& a, int grid, int block, int smem, cudaStream_t s) {
+    if (a.ng <= 1) k_trace<1, REC, EXT><<<grid, block, smem, s>>>(a);
+    else if (a.ng <= 3) k_trace<3, REC, EXT><<<grid, block, smem, s>>>(a);
+    else k_trace<4, REC, EXT><<<grid, block, smem, s>>>(a);
+}
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s) {
     const int smem = trace_smem_bytes(block, a.stack_log2);
+    const bool ext = a.rnext != nullptr || a.open != nullptr;
     if (a.recs != nullptr) {   // test aid: per-ray records (cell-visit counts)
-        if (a.ng <= 1) k_trace<1, true><<<grid, block, smem, s>>>(a);
-        else if (a.ng <= 3) k_trace<3, true><<<grid, block, smem, s>>>(a);
-        else k_trace<4, true><<<grid, block, smem, s>>>(a);
+        if (ext) launch_trace_ng<true, true>(a, grid, block, smem, s);
+        else launch_trace_ng<true, false>(a, grid, block, smem, s);
     } else {
-        if (a.ng <= 1) k_trace<1, false><<<grid, block, smem, s>>>(a);
-        else if (a.ng <= 3) k_trace<3, false><<<grid, block, smem, s>>>(a);
-        else k_trace<4, false><<<grid, block, smem, s>>>(a);
+        if (ext) launch_trace_ng<false, true>(a, grid, block, smem, s);
+        else launch_trace_ng<false, false>(a, grid, block, smem, s);
     }
+    return cudaGetLastError();
+}
+cudaError_t launch_thin_begin(Entry* seeds, int nseeds, const float* rthin, float* rnext, int nsrc,
+                              cudaStream_t s) {
+    const int work = max(nseeds, nsrc);
+    int blocks = (work + 255) / 256;
+    blocks = max(1, min(blocks, 152 * 4));
+    k_thin_begin<<<blocks, 256, 0, s>>>(seeds, nseeds, rthin, rnext, nsrc);
+    return cudaGetLastError();
+}
+cudaError_t launch_thin_fill(const ThinFillArgs& a, cudaStream_t s) {
+    if (a.nsrc <= 0) return cudaSuccess;
+    const dim3 grid(16, (unsigned)min(a.nsrc, 65535));
+    k_thin_fill<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_thin_commit(float* rthin, const float* rnext, int nsrc, cudaStream_t s) {
+    if (nsrc <= 0) return cudaSuccess;
+    k_thin_commit<<<(nsrc + 255) / 256, 256, 0, s>>>(rthin, rnext, nsrc);
     return cudaGetLastError();
 }
 cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s) {
     k_finalize<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding, double* out,
-                          cudaStream_t s) {
-    k_budget<<<1, 256, 0, s>>>(part, nparts, escaped, rounding, out);
+cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding,
+                          const double* thin, double* out, cudaStream_t s) {
+    k_budget<<<1, 256, 0, s>>>(part, nparts, escaped, rounding, thin, out);
     return cudaGetLastError();
 }
 

@@ -23,10 +23,14 @@ GAMMA_FLOOR = 1e-6
 
 
 def gpu_trace(w, xHI=None, xHeI=None, xHeII=None, records=False, rec_cap=1 << 22, dt=1.0,
-              tuning=None, params=None):
+              tuning=None, params=None, open_mask=None, thin_radii=None):
+    """thin_radii: run with the optically thin approximation from these radii
+    (Sec. 2.6); open_mask: emission mask [nsrc, 12*4^l_base] (Sec. 2.2)."""
     import torch
     import paper_1807_07094_gb300 as P
-    p = params or w.params()
+    p = dict(params or w.params())
+    if thin_radii is not None:
+        p["thin_approx"] = 1
     f32 = lambda a: np.ascontiguousarray(np.asarray(a, np.float32))
     xHI = w.xHI if xHI is None else xHI
     xHeI = w.xHeI if xHeI is None else xHeI
@@ -36,6 +40,10 @@ def gpu_trace(w, xHI=None, xHeI=None, xHeII=None, records=False, rec_cap=1 << 22
             a.set_tuning(*tuning)
         a.set_fields(f32(w.nH), f32(xHI), f32(xHeI), f32(xHeII), f32(w.T))
         a.add_sources(w.src_pos, w.src_ndot)
+        if open_mask is not None:
+            a.set_emission_mask(open_mask)
+        if thin_radii is not None:
+            a.set_thin_radii(thin_radii)
         buf = None
         if records:
             buf = torch.empty(rec_cap * P.REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
@@ -44,15 +52,19 @@ def gpu_trace(w, xHI=None, xHeI=None, xHeII=None, records=False, rec_cap=1 << 22
         g = g.cpu().numpy().astype(np.float64)
         h = h.cpu().numpy().astype(np.float64)
         st = a.stats()
+        r_thin = thin = None
+        if thin_radii is not None:
+            r_thin, thin = a.thin_radii(len(w.src_pos))
         recs = None
         if records:
             nrec = a.record_count()
             assert nrec <= rec_cap
             recs = buf[: nrec * P.REC_DTYPE.itemsize].cpu().numpy().view(P.REC_DTYPE)
-    return dict(gamma=g, heat=h, budget=b, stats=st, recs=recs)
+    return dict(gamma=g, heat=h, budget=b, stats=st, recs=recs, r_thin=r_thin, thin_photons=thin)
 
 
-def oracle_trace(w, xHI=None, xHeI=None, xHeII=None, records=False, params=None):
+def oracle_trace(w, xHI=None, xHeI=None, xHeII=None, records=False, params=None, open_mask=None,
+                 r_start=None):
     p = params or w.params()
     xHI = w.xHI if xHI is None else xHI
     xHeI = w.xHeI if xHeI is None else xHeI
@@ -60,7 +72,7 @@ def oracle_trace(w, xHI=None, xHeI=None, xHeII=None, records=False, params=None)
     # the oracle sees exactly the FP32 values the GPU gets
     d = lambda a: np.asarray(np.asarray(a, np.float32), np.float64)
     return oracle.trace(p, d(w.nH), d(xHI), d(xHeI), d(xHeII), w.src_pos, w.src_ndot,
-                        records=records)
+                        records=records, open_mask=open_mask, r_start=r_start)
 
 
 def geo_band(r, n):

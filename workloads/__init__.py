@@ -283,6 +283,30 @@ def subset_sources(w: Workload, idx) -> Workload:
     return dataclasses.replace(w, src_pos=w.src_pos[idx], src_ndot=w.src_ndot[idx])
 
 
+def ionised_bubbles(w: Workload, radius: float, x_in: float = 1e-4, xHeII_in: float = 0.05):
+    """The workload's gas with an ionised sphere of ``radius`` cells around
+    every source (x_HI = x_HeI = x_in, x_HeII = xHeII_in inside): the state the
+    optically thin approximation (Sec. 2.6) is made for.  Returns FP32
+    (xHI, xHeI, xHeII)."""
+    n = w.n
+    inside = np.zeros((n, n, n), bool)
+    r = int(np.ceil(radius)) + 1
+    for o in w.src_pos:
+        lo = np.maximum(np.floor(o).astype(int) - r, 0)
+        hi = np.minimum(np.floor(o).astype(int) + r + 1, n)
+        g = np.indices(tuple(hi - lo)).reshape(3, -1).T + lo
+        d2 = ((g + 0.5 - o) ** 2).sum(1)
+        g = g[d2 < radius * radius]
+        inside[g[:, 0], g[:, 1], g[:, 2]] = True
+    xHI = np.where(inside, x_in, w.xHI).astype(np.float32)
+    xHeI = np.where(inside, x_in, w.xHeI).astype(np.float32)
+    xHeII = np.where(inside, xHeII_in, w.xHeII).astype(np.float32)
+    if w.Y == 0:
+        xHeI[:] = 0
+        xHeII[:] = 0
+    return xHI, xHeI, xHeII
+
+
 def random_gas(n: int, seed: int, Y: float = 0.24, lo: float = 1e-4, hi: float = 1e-1):
     """Random gas state for chemistry tests: log-uniform nH, random fractions, T."""
     rng = np.random.Generator(np.random.PCG64(seed))
