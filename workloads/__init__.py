@@ -289,15 +289,18 @@ def ionised_bubbles(w: Workload, radius: float, x_in: float = 1e-4, xHeII_in: fl
     optically thin approximation (Sec. 2.6) is made for.  Returns FP32
     (xHI, xHeI, xHeII)."""
     n = w.n
-    inside = np.zeros((n, n, n), bool)
-    r = int(np.ceil(radius)) + 1
-    for o in w.src_pos:
-        lo = np.maximum(np.floor(o).astype(int) - r, 0)
-        hi = np.minimum(np.floor(o).astype(int) + r + 1, n)
-        g = np.indices(tuple(hi - lo)).reshape(3, -1).T + lo
-        d2 = ((g + 0.5 - o) ** 2).sum(1)
-        g = g[d2 < radius * radius]
-        inside[g[:, 0], g[:, 1], g[:, 2]] = True
+    if radius >= np.sqrt(3.0) * n:            # every cell is within reach of every source
+        inside = np.ones((n, n, n), bool)
+    else:
+        # distance from each cell centre to its nearest source, slab by slab
+        from scipy.spatial import cKDTree
+        tree = cKDTree(np.asarray(w.src_pos, np.float64))
+        jk = np.indices((n, n)).reshape(2, -1).T + 0.5
+        inside = np.zeros((n, n, n), bool)
+        for i in range(n):
+            pts = np.column_stack([np.full(n * n, i + 0.5), jk])
+            d, _ = tree.query(pts, distance_upper_bound=radius)
+            inside[i] = (d < radius).reshape(n, n)
     xHI = np.where(inside, x_in, w.xHI).astype(np.float32)
     xHeI = np.where(inside, x_in, w.xHeI).astype(np.float32)
     xHeII = np.where(inside, xHeII_in, w.xHeII).astype(np.float32)
