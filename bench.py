@@ -11,9 +11,14 @@ from pinned host memory and the new state copied out in every step.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload (the paper publishes no code; the oracle is the reference).
-For N > 1 the step runs as N independent replicas, one per rank (the tracer
-does not shard without a rate all-reduce), and rank 0 reports
-the aggregate.
+For N > 1 the step runs as N independent replicas, one per rank (sharding the
+tracer by source would leave every GPU with partial rate fields that need an
+all-reduce before the chemistry), and rank 0 reports the aggregate.
+
+``--memops`` measures the ceilings of the tracer's memory pattern and exits;
+``--thin RADIUS`` times traces with and without the optically thin
+approximation (Sec. 2.6) on the same field with ionised spheres of RADIUS cells
+around the sources and exits.
 """
 from __future__ import annotations
 
