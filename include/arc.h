@@ -362,7 +362,7 @@ arc_status arc_set_emission_mask(arc_ctx* ctx, const uint8_t* open, int64_t coun
  * and in the order sources were added.  A trace uses the current radii and
  * then replaces them with the ones it measured.  Adding or clearing sources
  * sets every radius to 0.  set: nsrc must equal the sources added, radii
- * finite and >= 0 (ARC_E_INVALID otherwise); synchronises.  get: radii
+ * in [0, 1e9] cells (ARC_E_INVALID otherwise); synchronises.  get: radii
  * (may be NULL) receives them; thin_photons (may be NULL) the photons the
  * thin fill deposited during the last trace, over its dt; synchronises.
  */

@@ -935,7 +935,8 @@ arc_status arc_set_thin_radii(arc_ctx* c, const double* radii, int nsrc) {
     if (!radii || nsrc != (int)c->hsrc.size())
         return fail(c, ARC_E_INVALID, "need one radius per source (%d)", (int)c->hsrc.size());
     for (int i = 0; i < nsrc; ++i)
-        if (!(radii[i] >= 0.0) || !isfinite(radii[i])) return fail(c, ARC_E_INVALID, "radius %d invalid", i);
+        if (!(radii[i] >= 0.0 && radii[i] <= 1e9))   // also keeps the FP32 copy finite
+            return fail(c, ARC_E_INVALID, "radius %d invalid (need 0 <= R <= 1e9 cells)", i);
     arc_status st = upload_sources(c);
     if (st != ARC_OK) return st;
     if (c->nsrc_dev == 0) return ARC_OK;
