@@ -192,16 +192,21 @@ def run_reference(args):
     w = W.cosmic_256()
     # each "step" is a bounded sample of the workload: ~ (60 s / (K+W)) of oracle time
     per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    vals = []
+    vals, step_ms = [], []
     for k in range(args.warmup + args.steps):
+        t0 = time.process_time()
         cb = cpu_baseline(w, per)
         if k >= args.warmup:
             vals.append(cb["value"])
+            step_ms.append(1e3 * (time.process_time() - t0))
     v = statistics.mean(vals)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+           "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+           "config": {"workload": WORKLOAD, "l2": "inputs larger than L2",
+                      "step": f"a bounded sample of the workload (~{per:.0f} s of oracle CPU time: "
+                              "sources in index order), timed on the host cores"},
            "cpu_baseline": dict(cb, value=v),
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
