@@ -369,6 +369,18 @@ arc_status arc_set_emission_mask(arc_ctx* ctx, const uint8_t* open, int64_t coun
 arc_status arc_set_thin_radii(arc_ctx* ctx, const double* radii, int nsrc);
 arc_status arc_get_thin_radii(arc_ctx* ctx, double* radii, int nsrc, double* thin_photons);
 
+/*
+ * arc_set_fault -- failure-detection test aid.  live_bias > 0 adds that many
+ * phantom unfinished rays to the tracer's count at the start of every trace,
+ * so the count never reaches zero and the warps, once out of work, wait for
+ * work that never comes; idle_timeout_s bounds that wait (default 10 s,
+ * 1 ms .. 60 s).  When the bound runs out the tracer sets its timeout status
+ * and returns; arc_trace then reports ARC_E_TIMEOUT (with a budget) and the
+ * context stays usable.  live_bias 0 restores normal tracing.  Applies to
+ * eager traces (arc_trace; the write uses a host value, not for capture).
+ */
+arc_status arc_set_fault(arc_ctx* ctx, int64_t live_bias, double idle_timeout_s);
+
 typedef struct arc_mlp_trainer arc_mlp_trainer;
 arc_status arc_mlp_trainer_create(arc_mlp_trainer** out, int max_batch, void* stream);
 /* copy in parameters (host, ARC_MLP_NPARAMS) and reset the AdamW state */

@@ -107,6 +107,7 @@ _SIGS = {
     "arc_set_emission_mask": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "arc_set_thin_radii": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "arc_get_thin_radii": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "arc_set_fault": ([C.c_void_p, C.c_int64, C.c_double], C.c_int),
 }
 
 MLP_NPARAMS = 9412
@@ -523,6 +524,10 @@ class Arc:
             return
         m = np.ascontiguousarray(np.asarray(open_mask, dtype=np.uint8).reshape(-1))
         _check(self.ctx, load().arc_set_emission_mask(C.c_void_p(self.ctx), m.ctypes.data, m.size))
+
+    def set_fault(self, live_bias: int = 0, idle_timeout_s: float = 10.0):
+        """Failure-detection test aid: phantom unfinished rays and the idle-wait bound."""
+        _check(self.ctx, load().arc_set_fault(C.c_void_p(self.ctx), int(live_bias), float(idle_timeout_s)))
 
     def set_thin_radii(self, radii):
         """Optically thin radius per source [cells] (Sec. 2.6, thin_approx)."""

@@ -82,6 +82,11 @@ struct arc_ctx {
     std::vector<uint8_t> hopen;
     uint8_t* dopen = nullptr;
     size_t dopen_cap = 0;
+    // failure-detection test aid (arc_set_fault): unfinished-ray count added at
+    // the start of every trace, the value written, and the idle-wait bound
+    long long fault_live_bias = 0;
+    long long fault_live_value = 0;
+    unsigned long long idle_timeout_ns = 10ull * 1000000000ull;
     // dynamic queue
     Entry* qdata = nullptr;
     unsigned long long* qseq = nullptr;
@@ -334,7 +339,7 @@ TraceArgs trace_args(arc_ctx* c) {
     a.nrec = &c->scal->nrec;
     a.rec_cap = (unsigned long long)c->rec_cap;
     a.stack_log2 = c->stack_log2;
-    a.idle_timeout_ns = 10ull * 1000000000ull;
+    a.idle_timeout_ns = c->idle_timeout_ns;
     return a;
 }
 
@@ -376,6 +381,13 @@ arc_status enqueue_trace(arc_ctx* c, int seeds_limit = 0) {
     TraceArgs A = trace_args(c);
     if (seeds_limit > 0 && seeds_limit < A.nseeds) A.nseeds = seeds_limit;
     CK(launch_seed_reset(A, c->qcap, A.nseeds, c->stream));
+    if (c->fault_live_bias != 0) {
+        // test aid: a count of unfinished rays that can never reach zero, so
+        // that idle warps wait for work that never comes (arc_set_fault)
+        c->fault_live_value = 4ll * A.nseeds + c->fault_live_bias;
+        CK(cudaMemcpyAsync(&c->scal->live, &c->fault_live_value, sizeof(long long), cudaMemcpyHostToDevice,
+                           c->stream));
+    }
     CK(record_event(c, c->ev[0]));
     if (c->p.thin_approx && c->nsrc_dev > 0) {
         // Sec. 2.6: rays start at each source's radius; the cells inside it
@@ -964,6 +976,16 @@ arc_status arc_get_thin_radii(arc_ctx* c, double* radii, int nsrc, double* thin_
             for (int i = 0; i < c->nsrc_dev; ++i) radii[c->dev_ids[i]] = (double)h[i];
     }
     if (thin_photons) *thin_photons = c->traced ? thin * PHOT_UNIT * c->last_dt : 0.0;
+    return ARC_OK;
+}
+
+arc_status arc_set_fault(arc_ctx* c, int64_t live_bias, double idle_timeout_s) {
+    if (!c) return ARC_E_INVALID;
+    if (live_bias < 0 || !(idle_timeout_s >= 1e-3 && idle_timeout_s <= 60.0))
+        return fail(c, ARC_E_INVALID, "need live_bias >= 0 and 1 ms <= idle_timeout_s <= 60 s");
+    c->fault_live_bias = live_bias;
+    c->idle_timeout_ns = (unsigned long long)(idle_timeout_s * 1e9);
+    c->graph_valid = false;
     return ARC_OK;
 }
 
