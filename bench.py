@@ -246,6 +246,48 @@ def surrogate_speedup(a, w, P, reps: int = 3):
             "weights": {"file": os.path.basename(P.SURROGATE_FILE), "samples": meta.get("samples")}}
 
 
+def side_timings(a, stream):
+    """The paper's other hot steps, timed with CUDA events on the context
+    stream: the Sec. 2.9 time-step reduction over the context's field, then
+    (after closing the context) ten graph-replayed steps of the Sec. 3.4 Test 3
+    clump at 128^3.  A failure is reported in the result, never raised."""
+    import torch
+    import paper_1807_07094_gb300 as P
+
+    side = {}
+    try:   # the call synchronises and copies the two minima back
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dt_n, dt_I = a.rt_timestep(0.1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        side["rt_timestep"] = {"ms": e0.elapsed_time(e1), "cells": a.n ** 3, "dt_n_s": dt_n, "dt_I_s": dt_I,
+                               "note": "includes the call's synchronisation and copy-back"}
+    except Exception as exc:  # noqa: BLE001
+        side["rt_timestep"] = {"error": str(exc)[:200]}
+    a.close()
+    try:
+        wc = W.clump_test3()
+        with P.Arc(wc.n, wc.box_cm, wc.params(), stream=stream.cuda_stream) as ac:
+            ac.set_fields(wc.nH, wc.xHI, wc.xHeI, wc.xHeII, wc.T)
+            ac.add_sources(wc.src_pos, wc.src_ndot)
+            for _ in range(3):
+                ac.step(wc.dt_s)
+            torch.cuda.synchronize()
+            s0 = ac.stats()["segments_total"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                ac.step(wc.dt_s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            side["test3_clump_128"] = {"ms_per_step": e0.elapsed_time(e1) / 10,
+                                       "segments_per_step": (ac.stats()["segments_total"] - s0) / 10}
+    except Exception as exc:  # noqa: BLE001
+        side["test3_clump_128"] = {"error": str(exc)[:200]}
+    return side
+
+
 def run_ours(args):
     import torch
     import paper_1807_07094_gb300 as P
@@ -332,39 +374,7 @@ def run_ours(args):
     t_e2e = max(time.perf_counter() - t0, 1e-9)
     segs_e2e = a.stats()["segments_total"] - segs_e0
 
-    # -------- the paper's other hot steps, timed on the side with CUDA events on
-    # the context stream (a failure here is reported, never fatal to the line)
-    side = {}
-    try:   # Sec. 2.9 time-step reduction over this field (the call synchronises)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dt_n, dt_I = a.rt_timestep(0.1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        side["rt_timestep"] = {"ms": e0.elapsed_time(e1), "cells": n3, "dt_n_s": dt_n, "dt_I_s": dt_I,
-                               "note": "includes the call's synchronisation and copy-back"}
-    except Exception as exc:  # noqa: BLE001
-        side["rt_timestep"] = {"error": str(exc)[:200]}
-    a.close()
-    try:   # Sec. 3.4 Test 3 clump (128^3, one source): graph-replayed steps
-        wc = W.clump_test3()
-        with P.Arc(wc.n, wc.box_cm, wc.params(), stream=stream.cuda_stream) as ac:
-            ac.set_fields(wc.nH, wc.xHI, wc.xHeI, wc.xHeII, wc.T)
-            ac.add_sources(wc.src_pos, wc.src_ndot)
-            for _ in range(3):
-                ac.step(wc.dt_s)
-            torch.cuda.synchronize()
-            s0 = ac.stats()["segments_total"]
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(10):
-                ac.step(wc.dt_s)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            side["test3_clump_128"] = {"ms_per_step": e0.elapsed_time(e1) / 10,
-                                       "segments_per_step": (ac.stats()["segments_total"] - s0) / 10}
-    except Exception as exc:  # noqa: BLE001
-        side["test3_clump_128"] = {"error": str(exc)[:200]}
+    side = side_timings(a, stream)   # closes a
 
     # max over ranks of the timed region, sum of work (replicas: weak scaling)
     dev = "cuda" if world > 1 and torch.distributed.get_backend() == "nccl" else "cpu"
