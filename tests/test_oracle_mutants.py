@@ -67,6 +67,7 @@ MUTANTS = [
     ("no split at the start", "if (r0 >= r_stop) {", "if (r0 > 1e30) {"),
     ("mask ignores the source", "opt->open[(int64_t)s * (int64_t)nrays + (int64_t)q]", "opt->open[(int64_t)q]"),
     ("blocked rays still emit", "c.nrec++;\n                continue;", "c.nrec++;"),
+    ("fill photons not booked", "                        tot += A;\n", "\n"),
 ]
 
 # fast pins first; a mutant is killed at the first failure
@@ -98,6 +99,7 @@ PINS = [
     TH.test_thin_fill_matches_traced_small_tau_limit,
     TH.test_complementary_masks_add_up,
     lambda: TH.test_single_open_pixel_lights_its_cone(22),
+    TH.test_thin_ledger_matches_the_cell_rates_with_helium,
 ]
 
 

@@ -193,3 +193,31 @@ def test_single_open_pixel_lights_its_cone(q):
     v = ((c - o) / np.linalg.norm(c - o, axis=1)[:, None] * g[:, None]).sum(0)
     assert oracle.vec2pix(1, v) == q
     assert abs(r["budget"][0] - 1e48 / 48) < 1e-12 * 1e48
+
+
+def test_thin_ledger_matches_the_cell_rates_with_helium():
+    """Photons absorbed in the cells, rebuilt from the per-absorber rates
+    (Gamma_s n_s V summed), equal the rays' absorbed photons plus the fill's
+    ledger, with three absorbers and three groups."""
+    import workloads as W
+    w = W.thermal_128(n=24, box_kpc=6.6 * 24 / 128)
+    w.src_pos = W.quantise_pos([[8.3, 12.7, 10.1], [15.5, 6.2, 17.75]])
+    w.src_ndot = np.vstack([w.src_ndot[0], 0.5 * w.src_ndot[0]])
+    xs = W.ionised_bubbles(w, 4.0)
+    d = lambda a: np.asarray(a, np.float64)
+    p = w.params()
+    r = oracle.trace(p, d(w.nH), *[d(x) for x in xs], w.src_pos, w.src_ndot, r_start=[3.5, 2.25])
+    em, ab, es = r["budget"]
+    assert abs(em - ab - es) < 1e-9 * em and r["thin_photons"] > 0
+    y = w.Y / (4 * (1 - w.Y))
+    nH = d(w.nH)
+    ns = np.stack([nH * d(xs[0]), y * nH * d(xs[1]), y * nH * d(xs[2])])
+    cells = (r["gamma"] * ns).sum() * (w.box_cm / w.n) ** 3
+    assert abs(cells - (ab + r["thin_photons"])) < 1e-9 * cells
+
+
+def test_masks_and_thin_radii_are_refused_together():
+    n = 16
+    p = uniform_params(n, 0.1)
+    with pytest.raises(ValueError):
+        _trace(p, n, 1.0, (8.3, 8.6, 8.1), r_start=[2.0], open_mask=np.ones((1, 48), bool))
