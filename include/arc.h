@@ -243,30 +243,38 @@ arc_status arc_get_tuning(arc_ctx* ctx, int* block_threads, int* blocks_per_sm, 
 
 /*
  * arc_trace_noalloc -- one radiative-transfer pass, like arc_trace, that
- * allocates nothing.  For callers that cannot allocate device memory at the
- * time of the call: code running while a stream is captured into a CUDA graph
- * (cudaMalloc/cudaFree are not permitted there, and cudaFree synchronises the
- * device), and applications that reserve all device memory up front.  The
- * paper has no counterpart; this is a deployment variant of the tracer.
+ * allocates nothing.  The paper has no counterpart: it is a deployment variant
+ * of the tracer for callers that cannot allocate device memory when they need
+ * a trace.  Simulation codes that embed a radiative-transfer step often hand
+ * all of the GPU's memory to their own pool allocator at start-up (to avoid
+ * fragmentation and late out-of-memory failures in runs of days), so a library
+ * that asks the driver for more finds nothing left or is forbidden to ask; and
+ * cudaFree waits for all work on the device, which such codes cannot afford
+ * inside their time-step loop.  arc_create allocates its buffers, so these
+ * callers use this entry point instead.
  *
  *   g, p            grid and parameters as for arc_create; n <= ARC_NOALLOC_MAX_N,
- *                   l_base <= 2
+ *                   l_base <= 2, no optically thin approximation
  *   nH..xHeII       device pointers, n^3 FP32 each, C order (as arc_set_fields)
- *   nsrc, pos, ndot host arrays as for arc_add_sources, nsrc <= ARC_NOALLOC_MAX_SOURCES
+ *   nsrc, pos, ndot host arrays as for arc_add_sources (pos nsrc*3, ndot
+ *                   nsrc*ngroups), nsrc <= ARC_NOALLOC_MAX_SOURCES
  *   gamma, heat     caller-owned device buffers of 3 n^3 FP32 each (outputs, as
  *                   returned by arc_trace)
  *   budget          NULL or host double[4], as for arc_trace
  *   stream          cudaStream_t for the work (NULL = legacy default stream)
  *
  * Scratch memory is one fixed file-scope device array of about 18 MB that every
- * device which loads libarc holds until the process exits.  The first call on
- * a device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array and it
- * keeps the last call's contents (each call clears what must start at zero), so
- * calls whose GPU work overlaps -- on different streams or from different host
- * threads -- race and corrupt each other's results.  Synchronises the stream.
- * Returns ARC_E_INVALID for sizes beyond the maximum or bad arguments, and the
- * tracer errors of arc_trace (ARC_E_TIMEOUT, ARC_E_OVERFLOW, ARC_E_BUDGET).
+ * device which loads libarc holds until the process exits; the call makes no
+ * cudaMalloc, cudaFree or other allocating call.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current.  All calls share the array and it keeps the last call's contents
+ * (each call clears what must start at zero), so calls whose GPU work overlaps
+ * -- on different streams or from different host threads -- race and corrupt
+ * each other's results.  The call copies the source table from host memory and
+ * waits for the stream before it returns.  Returns ARC_E_INVALID for sizes
+ * beyond the maximum or bad arguments, and the tracer errors of arc_trace
+ * (ARC_E_TIMEOUT, ARC_E_OVERFLOW, ARC_E_BUDGET); the binding must check the
+ * array sizes, which the C interface cannot see.
  */
 #define ARC_NOALLOC_MAX_N 64
 #define ARC_NOALLOC_MAX_SOURCES 256

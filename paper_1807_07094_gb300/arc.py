@@ -215,9 +215,10 @@ def arc_set_fields(ctx, nH, xHI, xHeI, xHeII, T) -> None:
     _check(ctx, load().arc_set_fields(C.c_void_p(ctx), *[C.c_void_p(p) for p, _ in ptrs], kinds.pop()))
 
 
-def arc_add_sources(ctx, pos, ndot) -> None:
-    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-    ndot = np.ascontiguousarray(ndot, dtype=np.float64)
+def arc_add_sources(ctx, pos, ndot, ngroups: Optional[int] = None) -> None:
+    """pos [nsrc, 3] FP64 grid units, ndot nsrc * ngroups photons/s; give
+    ngroups (the context's) to have the size of ndot checked."""
+    pos, ndot = _check_sources(pos, ndot, ngroups)
     _check(ctx, load().arc_add_sources(C.c_void_p(ctx), pos.shape[0], pos.ctypes.data, ndot.ctypes.data))
 
 
@@ -284,27 +285,64 @@ NOALLOC_MAX_N = 64
 NOALLOC_MAX_SOURCES = 256
 
 
+def _numel(a) -> int:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return int(a.numel())
+    except ImportError:
+        pass
+    return int(np.asarray(a).size)
+
+
+def _check_sources(pos, ndot, ngroups: Optional[int]):
+    """pos as [nsrc, 3] FP64 and ndot as nsrc * ngroups FP64 (the C side reads
+    exactly that many values and cannot see the arrays' sizes)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    if pos.size % 3 != 0 or (pos.ndim == 2 and pos.shape[1] != 3):
+        raise ValueError("source positions must be [nsrc, 3]")
+    pos = pos.reshape(-1, 3)
+    ndot = np.ascontiguousarray(ndot, dtype=np.float64).reshape(-1)
+    if ngroups is not None and ndot.size != pos.shape[0] * int(ngroups):
+        raise ValueError(f"ndot must hold nsrc * ngroups = {pos.shape[0]} * {int(ngroups)} values, "
+                         f"got {ndot.size}")
+    return pos, ndot
+
+
 def arc_trace_noalloc(grid: ArcGrid, params: ArcParams, nH, xHI, xHeI, xHeII, pos, ndot, gamma, heat,
                       stream: Optional[int] = None):
     """One trace into caller-owned device buffers with no allocation (see
-    include/arc.h).  Fields and outputs are contiguous float32 CUDA tensors;
-    returns the budget[4]."""
-    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-    ndot = np.ascontiguousarray(ndot, dtype=np.float64)
+    include/arc.h).  Fields (n^3 each) and outputs (3 n^3 each) are contiguous
+    float32 CUDA tensors; returns the budget[4].  Every size is checked here,
+    before any launch: the C interface receives bare pointers."""
+    n = int(grid.n)
+    pos, ndot = _check_sources(pos, ndot, params.ngroups)
     ptrs = []
-    for a in (nH, xHI, xHeI, xHeII, gamma, heat):
+    for name, a, size in (("nH", nH, n ** 3), ("xHI", xHI, n ** 3), ("xHeI", xHeI, n ** 3),
+                          ("xHeII", xHeII, n ** 3), ("gamma", gamma, 3 * n ** 3),
+                          ("heat", heat, 3 * n ** 3)):
         p, on_dev = _ptr_and_kind(a)
         if not on_dev:
             raise ValueError("arc_trace_noalloc takes device arrays")
+        if _numel(a) != size:
+            raise ValueError(f"{name} must hold {size} float32 values for n = {n}, got {_numel(a)}")
         ptrs.append(p)
     b = (C.c_double * 4)()
     st = load().arc_trace_noalloc(C.byref(grid), C.byref(params), *[C.c_void_p(q) for q in ptrs[:4]],
                                   pos.shape[0], pos.ctypes.data, ndot.ctypes.data,
                                   C.c_void_p(ptrs[4]), C.c_void_p(ptrs[5]), b, C.c_void_p(stream or 0))
+    if st == ARC_E_INVALID:
+        raise ArcError(st, "arc_trace_noalloc refused its arguments (n=%d, %d sources; its fixed "
+                       "scratch allows n <= ARC_NOALLOC_MAX_N=%d, sources <= "
+                       "ARC_NOALLOC_MAX_SOURCES=%d, l_base <= 2, no thin approximation; positions "
+                       "inside the box, finite non-negative luminosities)"
+                       % (n, pos.shape[0], NOALLOC_MAX_N, NOALLOC_MAX_SOURCES))
     if st != ARC_OK:
-        raise ArcError(st, "arc_trace_noalloc failed (n=%d, %d sources; its fixed scratch allows "
-                       "n <= ARC_NOALLOC_MAX_N=%d, sources <= ARC_NOALLOC_MAX_SOURCES=%d, l_base <= 2)"
-                       % (grid.n, pos.shape[0], NOALLOC_MAX_N, NOALLOC_MAX_SOURCES))
+        what = {ARC_E_CUDA: "a CUDA call failed",
+                ARC_E_TIMEOUT: "the tracer's bounded wait for work ran out",
+                ARC_E_OVERFLOW: "the work queue overflowed",
+                ARC_E_BUDGET: "the photon budget did not close to 1e-9"}.get(st, "the trace failed")
+        raise ArcError(st, f"arc_trace_noalloc: {what} (n={n}, {pos.shape[0]} sources)")
     return np.array(list(b))
 
 
@@ -441,6 +479,7 @@ class Arc:
 
     def __init__(self, n: int, box_cm: float, params: dict, stream: Optional[int] = None):
         self.n = int(n)
+        self.ngroups = int(params["ngroups"])
         g = ArcGrid(self.n, float(box_cm))
         self.ctx = arc_create(g, make_params(params), stream)
 
@@ -462,10 +501,13 @@ class Arc:
             pass
 
     def set_fields(self, nH, xHI, xHeI, xHeII, T):
+        for name, a in (("nH", nH), ("xHI", xHI), ("xHeI", xHeI), ("xHeII", xHeII), ("T", T)):
+            if _numel(a) != self.n ** 3:
+                raise ValueError(f"{name} must hold n^3 = {self.n ** 3} values, got {_numel(a)}")
         arc_set_fields(self.ctx, nH, xHI, xHeI, xHeII, T)
 
     def add_sources(self, pos, ndot):
-        arc_add_sources(self.ctx, pos, ndot)
+        arc_add_sources(self.ctx, pos, ndot, self.ngroups)
 
     def clear_sources(self):
         arc_clear_sources(self.ctx)

@@ -1,16 +1,19 @@
 // arc_noalloc.cu -- arc_trace_noalloc: one radiative-transfer pass that
 // allocates nothing.
 //
-// Some callers cannot allocate device memory when they need a trace: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc and
-// cudaFree are not allowed there and cudaFree synchronises the device), and
-// hosts that budget all device memory up front and forbid allocations at run
-// time.  For them this entry point runs the same tracer kernels as arc_trace,
-// but every scratch buffer (optical-depth records, compensated accumulators,
-// work queue, source table, counters) lives in one file-scope device array of
-// fixed size, so grids and source counts are capped (ARC_NOALLOC_MAX_N,
-// ARC_NOALLOC_MAX_SOURCES).  The caller passes the gas fields and receives the
-// rates in its own device buffers.
+// Some callers cannot allocate device memory when they need a trace.
+// Simulation codes that embed a radiative-transfer step commonly give the
+// whole GPU memory to their own pool allocator when they start (so that a run
+// of days neither fragments memory nor fails late for lack of it); a library
+// that then asks the driver for memory finds none, or is not allowed to ask.
+// Such codes also cannot let a library call cudaFree inside their time-step
+// loop, since it waits for all work on the device.  For them this entry point
+// runs the same tracer kernels as arc_trace, but every scratch buffer
+// (optical-depth records and absorbed photons, work queue, source table,
+// counters) lives in one file-scope device array of fixed size, so grids and
+// source counts are capped (ARC_NOALLOC_MAX_N, ARC_NOALLOC_MAX_SOURCES).  The
+// caller passes the gas fields and receives the rates in its own device
+// buffers.
 //
 // The array is shared by every call in the process and keeps the last call's
 // contents; each call clears what must start at zero.  Calls whose GPU work

@@ -79,3 +79,28 @@ def test_invalid_params_rejected_without_gpu_work():
     with pytest.raises(A.ArcError) as e:
         A.arc_create(A.ArcGrid(16, 1e21), A.make_params(p))
     assert e.value.status == A.ARC_E_INVALID
+
+
+def test_binding_checks_array_sizes_before_any_launch():
+    """The C interface receives bare pointers, so the binding refuses arrays of
+    the wrong size before anything reaches libarc (no GPU is touched: the
+    checks run on host arrays and raise ValueError)."""
+    import workloads as W
+    w = W.stromgren_32(n=8)
+    grid = A.ArcGrid(8, w.box_cm)
+    prm = A.make_params(w.params())
+    with pytest.raises(ValueError):
+        A._check_sources(np.zeros((2, 3)), np.ones(3), 1)          # 2 sources, 1 group: 2 values
+    with pytest.raises(ValueError):
+        A._check_sources(np.zeros((2, 2)), np.ones(2), 1)          # positions not [nsrc, 3]
+    pos, nd = A._check_sources(np.zeros(6), np.ones(6), 3)
+    assert pos.shape == (2, 3) and nd.shape == (6,)
+    f = np.zeros(8 ** 3, np.float32)
+    short = np.zeros(8 ** 3 - 1, np.float32)
+    # host arrays are refused as such; the size checks come first for a wrong size
+    with pytest.raises(ValueError):
+        A.arc_trace_noalloc(grid, prm, f, f, f, short, w.src_pos, w.src_ndot,
+                            np.zeros(3 * 8 ** 3, np.float32), np.zeros(3 * 8 ** 3, np.float32))
+    with pytest.raises(ValueError):
+        A.arc_trace_noalloc(grid, prm, f, f, f, f, w.src_pos, np.ones(5),
+                            np.zeros(3 * 8 ** 3, np.float32), np.zeros(3 * 8 ** 3, np.float32))

@@ -4,25 +4,38 @@ The host adds phantom unfinished rays (arc_set_fault), so the tracer's count of
 live rays never reaches zero and its warps, once out of work, wait for work that
 never comes.  With a 0.2 s bound the wait runs out, the kernel sets its timeout
 status and returns; the trace reports ARC_E_TIMEOUT, and the same context then
-traces normally again."""
+traces normally again.
+
+"Normally" is judged the way every rate comparison is: the trace after the
+timeout matches the FP64 oracle to 1e-4 where Gamma exceeds 1e-6 of its maximum
+(Sec. 2.4, Eq. ion), closes its photon budget to 1e-9, and agrees with the trace
+before the fault to 1e-5.  Each cell's Gamma is an FP32 sum of returning vector
+atomics from many lanes, so the order of the additions (and the last bits of the
+sum) changes from launch to launch; the ray trees, segment counts and the
+budget do not depend on that order and are compared exactly."""
 import time
 
 import numpy as np
 import pytest
 
 import workloads as W
+from helpers import GAMMA_FLOOR, GAMMA_RTOL, oracle_trace, rate_errors
 
 pytestmark = pytest.mark.gpu
+
+ATOMIC_ORDER_RTOL = 1e-5
 
 
 def test_idle_wait_runs_out_and_the_context_recovers():
     import paper_1807_07094_gb300 as P
     w = W.stromgren_32()
+    o = oracle_trace(w)
     with P.Arc(w.n, w.box_cm, w.params()) as a:
         a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
         a.add_sources(w.src_pos, w.src_ndot)
         g0, _, b0 = a.trace(1.0)
-        g0 = g0.cpu().numpy().copy()
+        g0 = g0.cpu().numpy().astype(np.float64)
+        s0 = a.stats()
         a.set_fault(live_bias=1, idle_timeout_s=0.2)
         t = time.time()
         with pytest.raises(P.ArcError) as e:
@@ -32,5 +45,16 @@ def test_idle_wait_runs_out_and_the_context_recovers():
         assert a.stats()["error_word"] & 1            # the kernel's timeout bit
         a.set_fault(0, 10.0)
         g1, _, b1 = a.trace(1.0)
-        assert np.array_equal(g1.cpu().numpy(), g0)   # all rays were traced both times
-        assert abs(b1[0] - b1[1] - b1[2]) <= 1e-9 * b1[0]
+        g1 = g1.cpu().numpy().astype(np.float64)
+        s1 = a.stats()
+    # every ray was traced again: same tree, same segments
+    assert s1["segments"] == s0["segments"] and s1["rays"] == s0["rays"]
+    assert s1["max_level"] == s0["max_level"]
+    assert abs(b1[0] - b1[1] - b1[2]) <= 1e-9 * b1[0]
+    assert abs(b1[0] - b0[0]) <= 1e-12 * b0[0]        # launched photons: no atomics involved
+    # rates against the oracle at the usual bar
+    for rel, cnt, worst in rate_errors(g1, o["gamma"])[:1]:
+        assert cnt > 0 and rel <= GAMMA_RTOL, worst
+    # and against the first trace at the bar for reordered FP32 atomic sums
+    m = g0[0] > GAMMA_FLOOR * g0[0].max()
+    assert np.max(np.abs(g1[0][m] - g0[0][m]) / g0[0][m]) <= ATOMIC_ORDER_RTOL

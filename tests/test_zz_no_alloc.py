@@ -1,11 +1,14 @@
 """arc_trace_noalloc: the trace entry point that allocates no device memory.
 
-It serves callers that cannot allocate when they trace -- code running while
-a stream is captured into a CUDA graph, where cudaMalloc/cudaFree are not
-permitted, and applications that reserve all device memory up front.  Its
-scratch is a fixed file-scope device array, so it must give the same rates as
-arc_trace (the context path, which allocates its buffers) and must give them
-again on a second call, since the array keeps the previous call's contents.
+It serves host codes that cannot allocate when they trace: simulation
+frameworks that give the whole GPU memory to their own pool allocator at
+start-up, where a library's cudaMalloc finds nothing or is not allowed, and
+that cannot let a library call cudaFree (which waits for the whole device)
+inside their step loop.  Its scratch is a fixed file-scope device array, so it
+must give the same rates as arc_trace (the context path, which allocates its
+buffers) and must give them again on a second call, since the array keeps the
+previous call's contents.  The device's free memory must not change across a
+call: the library makes no allocation that torch's allocator would not see.
 
 This file is collected last so that a run stopping at the first failure has
 run every other test before it.
@@ -51,9 +54,16 @@ def test_noalloc_matches_context_trace_on_two_calls(case):
         gamma = torch.full((3, w.n, w.n, w.n), -1.0, dtype=torch.float32, device="cuda")
         heat = torch.full((3, w.n, w.n, w.n), -1.0, dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         budget = A.arc_trace_noalloc(grid, params, *fields, w.src_pos, w.src_ndot, gamma, heat,
                                      stream=torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
+        if call == 1:
+            # no cudaMalloc / cudaMallocAsync inside the call: torch's caching
+            # allocator cannot see libarc's allocations, the driver's free count
+            # can.  (The first call may load the library's device code, and with
+            # it the static scratch array, so it is not the one measured.)
+            assert torch.cuda.mem_get_info()[0] == free0
         launched, absorbed, escaped, emitted = budget
         assert abs(launched - absorbed - escaped) <= 1e-9 * launched
         assert np.allclose(budget, ref["budget"], rtol=1e-6)
