@@ -15,7 +15,6 @@ For N > 1 the step runs as N independent replicas, one per rank (sharding the
 tracer by source would leave every GPU with partial rate fields that need an
 all-reduce before the chemistry), and rank 0 reports the aggregate.
 
-``--memops`` measures the ceilings of the tracer's memory pattern and exits;
 ``--thin RADIUS`` times traces with and without the optically thin
 approximation (Sec. 2.6) on the same field with ionised spheres of RADIUS cells
 around the sources and exits.
@@ -420,20 +419,6 @@ def run_ours(args):
     return 0
 
 
-def run_memops():
-    """Throughput ceilings of the tracer's per-segment memory pattern (random
-    32-byte cell records: 16-byte load, 16-byte vector atomic, both) on this
-    GPU; context for the roofline fraction."""
-    import paper_1807_07094_gb300.build as B
-    src = os.path.join(ROOT, "paper_1807_07094_gb300", "probe", "memops.cu")
-    exe = os.path.join(B.LIBDIR, "memops")
-    os.makedirs(B.LIBDIR, exist_ok=True)
-    subprocess.run([B.nvcc(), *B.ARCH, "-O3", "-o", exe, src], check=True)
-    r = subprocess.run([exe], capture_output=True, text=True)
-    sys.stdout.write(r.stdout)
-    return r.returncode
-
-
 def run_thin(args):
     """The optically thin approximation (Sec. 2.6) on the benchmark field: every
     source in an ionised sphere of args.thin cells, traced with the
@@ -508,16 +493,12 @@ def main():
                     help="cosmic_256 (256^3 x 1000 sources, the benchmark) or cosmic_512 (512^3 x 10^4)")
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the e2e pass")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-vs-ODE chemistry comparison")
-    ap.add_argument("--memops", action="store_true",
-                    help="measure the memory-operation ceilings of the tracer's access pattern and exit")
     ap.add_argument("--thin", type=float, default=0.0,
                     help="time traces with and without the optically thin approximation on the benchmark "
                          "field with ionised spheres of this radius [cells] around the sources, and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.memops:
-        return run_memops()
     if args.thin > 0:
         return run_thin(args)
     if args.impl == "reference":
