@@ -130,6 +130,8 @@ def lib(path: Optional[str] = None):
         L.orc_cooling.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double, C.c_double]
         L.orc_cooling.restype = C.c_double
+        L.orc_cooling_terms.argtypes = L.orc_cooling.argtypes + [dp]
+        L.orc_cooling_terms.restype = None
         _lib = L
     return _lib
 
@@ -267,6 +269,18 @@ def rates(params: dict, T: float) -> np.ndarray:
 def cooling(params: dict, T, nH, nHI, nHeI, nHeII, ne) -> float:
     p = make_params(params)
     return float(lib().orc_cooling(C.byref(p), T, nH, nHI, nHeI, nHeII, ne))
+
+
+COOLING_TERMS = ("ci_HI", "ci_HeI", "ci_HeII", "rec_HII", "rec_HeII", "rec_HeIII", "diel_HeII",
+                 "exc_HI", "exc_HeII", "ff", "compton")
+
+
+def cooling_terms(params: dict, T, nH, nHI, nHeI, nHeII, ne) -> dict:
+    """The cooling rate's terms one by one [erg/s/cm^3], named as COOLING_TERMS."""
+    p = make_params(params)
+    out = np.zeros(len(COOLING_TERMS))
+    lib().orc_cooling_terms(C.byref(p), T, nH, nHI, nHeI, nHeII, ne, _dptr(out))
+    return dict(zip(COOLING_TERMS, out.tolist()))
 
 
 def run(params: dict, w, nsteps: int, trace_every: int = 1):

@@ -571,7 +571,11 @@ int orc_trace_opt(const orc_params* p, const double* nH, const double* xHI,
 /* Rate fits: Hui & Gnedin (1997) case-B recombination, collisional          */
 /* ionisation and recombination cooling; Cen (1992) collisional excitation,  */
 /* dielectronic recombination and free-free Gaunt factor; Compton cooling    */
-/* off the CMB from Thomson scattering.                                       */
+/* off the CMB from Thomson scattering.  Pinned against published atomic     */
+/* physics, not against these fits (tests/test_oracle_rates.py): tabulated   */
+/* case-B coefficients, an independent collisional-ionisation fit, the mean  */
+/* energy per recombination, hydrogenic scaling, line and ionisation         */
+/* energies, collision strengths and the free-free coefficient.              */
 /* ------------------------------------------------------------------------- */
 #define T_HI 157807.0
 #define T_HEI 285335.0
@@ -603,8 +607,13 @@ void orc_rates(const orc_params* p, double T, double out[6]) {
     }
 }
 
-double orc_cooling(const orc_params* p, double T, double nH, double nHI, double nHeI,
-                   double nHeII, double ne) {
+/* Cooling terms [erg cm^-3 s^-1], one per process (ORC_NCOOL entries, order of
+ * orc_cooling_terms in arc_oracle.h): collisional ionisation of HI, HeI, HeII;
+ * recombination of HII (case B), HeII (radiative), HeIII (case B); dielectronic
+ * recombination of HeII; collisional excitation of HI and HeII; free-free;
+ * Compton scattering off the CMB. */
+void orc_cooling_terms(const orc_params* p, double T, double nH, double nHI, double nHeI,
+                       double nHeII, double ne, double L[ORC_NCOOL]) {
     const double y = p->Y / (4.0 * (1.0 - p->Y));
     const double nHe = y * nH;
     const double nHII = nH - nHI;
@@ -614,27 +623,41 @@ double orc_cooling(const orc_params* p, double T, double nH, double nHI, double 
     double r[6];
     orc_rates(p, T, r);
     /* collisional ionisation: threshold energy per ionisation */
-    double L = ne * (r[3] * nHI * KB * T_HI + r[4] * nHeI * KB * T_HEI + r[5] * nHeII * KB * T_HEII);
+    L[0] = ne * r[3] * nHI * KB * T_HI;
+    L[1] = ne * r[4] * nHeI * KB * T_HEI;
+    L[2] = ne * r[5] * nHeII * KB * T_HEII;
     /* recombination (case B) and dielectronic recombination */
-    L += ne * (hg_recool_b(T, lHI) * nHII +
-               1.26e-14 * pow(lHeI, 0.750) * KB * T * nHeII +
-               8.0 * hg_recool_b(T, lHeII) * nHeIII +
-               1.24e-13 * pow(T, -1.5) * exp(-4.7e5 / T) * (1.0 + 0.3 * exp(-9.4e4 / T)) * nHeII);
+    L[3] = ne * hg_recool_b(T, lHI) * nHII;
+    L[4] = ne * 1.26e-14 * pow(lHeI, 0.750) * KB * T * nHeII;
+    /* HeIII is hydrogenic (Z = 2): Lambda(Z, T) = Z^3 Lambda_HII(T / Z^2), the
+     * fit's temperature prefactor taken at the scaled temperature whose lambda
+     * is lHeII */
+    L[5] = ne * 8.0 * hg_recool_b(T * (T_HI / T_HEII), lHeII) * nHeIII;
+    L[6] = ne * 1.24e-13 * pow(T, -1.5) * exp(-4.7e5 / T) * (1.0 + 0.3 * exp(-9.4e4 / T)) * nHeII;
     /* collisional excitation */
     const double sq = 1.0 + sqrt(T / 1e5);
-    L += ne * (7.5e-19 * exp(-118348.0 / T) / sq * nHI +
-               5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) / sq * nHeII);
+    L[7] = ne * 7.5e-19 * exp(-118348.0 / T) / sq * nHI;
+    L[8] = ne * 5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) / sq * nHeII;
     /* bremsstrahlung */
     const double lg = log10(T) - 5.5;
     const double gff = 1.1 + 0.34 * exp(-lg * lg / 3.0);
-    L += 1.42e-27 * gff * sqrt(T) * (nHII + nHeII + 4.0 * nHeIII) * ne;
+    L[9] = 1.42e-27 * gff * sqrt(T) * (nHII + nHeII + 4.0 * nHeIII) * ne;
     /* Compton scattering off the CMB: 4 sigma_T a k / (m_e c) T_g^4 (T - T_g) n_e */
+    L[10] = 0.0;
     if (p->z_compton >= 0.0) {
         const double sigT = 6.6524587e-25, arad = 7.5657e-15, me = 9.1093837e-28, cl = 2.99792458e10;
         const double Tg = 2.725 * (1.0 + p->z_compton);
-        L += 4.0 * sigT * arad * KB / (me * cl) * Tg * Tg * Tg * Tg * (T - Tg) * ne;
+        L[10] = 4.0 * sigT * arad * KB / (me * cl) * Tg * Tg * Tg * Tg * (T - Tg) * ne;
     }
-    return L;
+}
+
+double orc_cooling(const orc_params* p, double T, double nH, double nHI, double nHeI,
+                   double nHeII, double ne) {
+    double L[ORC_NCOOL];
+    orc_cooling_terms(p, T, nH, nHI, nHeI, nHeII, ne, L);
+    double s = 0.0;
+    for (int k = 0; k < ORC_NCOOL; k++) s += L[k];
+    return s;
 }
 
 /* The sub-cycled update; min_sub > 0 also caps every sub-step at dt / min_sub

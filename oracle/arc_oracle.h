@@ -159,9 +159,16 @@ void orc_rt_timestep(const orc_params* p, int64_t ncell, const double* nH, const
  * out[0..5] = alpha_HII, alpha_HeII(+dielectronic), alpha_HeIII,
  *             beta_HI, beta_HeI, beta_HeII  [cm^3/s]. */
 void orc_rates(const orc_params* p, double T, double out[6]);
-/* Net cooling minus heating pieces for a state: out[0] = Lambda [erg/s/cm^3]. */
+/* Cooling rate Lambda [erg/s/cm^3] of a state: the sum of the terms below. */
 double orc_cooling(const orc_params* p, double T, double nH, double nHI, double nHeI,
                    double nHeII, double ne);
+/* The cooling terms one by one [erg/s/cm^3] (for tests): collisional ionisation
+ * of HI, HeI, HeII; recombination of HII (case B), HeII (radiative), HeIII (case
+ * B); dielectronic recombination of HeII; collisional excitation of HI, HeII;
+ * free-free; Compton. */
+#define ORC_NCOOL 11
+void orc_cooling_terms(const orc_params* p, double T, double nH, double nHI, double nHeI,
+                       double nHeII, double ne, double L[ORC_NCOOL]);
 
 #ifdef __cplusplus
 }

@@ -94,8 +94,10 @@ __device__ __forceinline__ float cooling_per_h(float T, float nH, float a0, floa
     const float a3 = fmaxf(C.y - a1 - a2, 0.0f);          // HeIII per H
     const float nxe = nH * xe;                             // n_e [cm^-3]
     float L = r.b0 * a0 * (KB * TH_HI) + r.b1 * a1 * (KB * TH_HEI) + r.b2 * a2 * (KB * TH_HEII);
+    // HeIII recombination is hydrogenic (Z = 2): Z^3 times the HII cooling at
+    // T / Z^2, i.e. the fit at lHeII with its temperature prefactor scaled
     L += hg_recool<M>(T, lHI) * aHII + 1.26e-14f * M::pow(lHeI, 0.750f) * KB * T * a2 +
-         8.0f * hg_recool<M>(T, lHeII) * a3 + 1.24e-13f * dielectronic_shape<M>(T) * a2;
+         8.0f * hg_recool<M>(T * (TH_HI / TH_HEII), lHeII) * a3 + 1.24e-13f * dielectronic_shape<M>(T) * a2;
     const float sq = 1.0f + sqrtf(T * 1e-5f);
     L += 7.5e-19f * M::exp(-118348.0f / T) / sq * a0 + 5.54e-17f * M::pow(T, -0.397f) * M::exp(-473638.0f / T) / sq * a2;
     const float lg = M::lg10(T) - 5.5f;

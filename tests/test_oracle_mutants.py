@@ -13,6 +13,7 @@ import pytest
 import oracle
 import test_oracle_chem as CH
 import test_oracle_healpix as HP
+import test_oracle_rates as RT
 import test_oracle_thin as TH
 import test_oracle_trace as TR
 
@@ -68,10 +69,38 @@ MUTANTS = [
     ("mask ignores the source", "opt->open[(int64_t)s * (int64_t)nrays + (int64_t)q]", "opt->open[(int64_t)q]"),
     ("blocked rays still emit", "c.nrec++;\n                continue;", "c.nrec++;"),
     ("fill photons not booked", "                        tot += A;\n", "\n"),
+    # rate coefficients and cooling (Sec. 2.8): one planted typo per coefficient family
+    ("HeII radiative coefficient", "out[1] = 1.26e-14 * pow(lHeI, 0.750) +", "out[1] = 1.62e-14 * pow(lHeI, 0.750) +"),
+    ("dielectronic threshold", "1.90e-3 * pow(T, -1.5) * exp(-4.7e5 / T)", "1.90e-3 * pow(T, -1.5) * exp(-7.4e5 / T)"),
+    ("dielectronic prefactor", "1.90e-3 * pow(T, -1.5)", "1.09e-3 * pow(T, -1.5)"),
+    ("HeIII alpha not doubled", "out[2] = 2.0 * hg_alpha_b(lHeII);", "out[2] = hg_alpha_b(lHeII);"),
+    ("HI collisional exponent", "pow(1.0 + pow(lHI / 0.354, 0.874), 1.101)", "pow(1.0 + pow(lHI / 0.354, 0.874), 1.01)"),
+    ("HeI collisional coefficient", "32.38 * t32", "23.38 * t32"),
+    ("HeII collisional scale", "lHeII / 0.553", "lHeII / 5.53"),
+    ("HII recombination cooling exponent", "3.435e-30 * T * pow(lam, 1.970)", "3.435e-30 * T * pow(lam, 1.907)"),
+    ("HeII recombination cooling without kT", "L[4] = ne * 1.26e-14 * pow(lHeI, 0.750) * KB * T * nHeII;",
+     "L[4] = ne * 1.26e-14 * pow(lHeI, 0.750) * KB * 1e4 * nHeII;"),
+    ("HeIII recombination cooling unscaled", "hg_recool_b(T * (T_HI / T_HEII), lHeII)", "hg_recool_b(T, lHeII)"),
+    ("dielectronic cooling coefficient", "L[6] = ne * 1.24e-13", "L[6] = ne * 1.42e-13"),
+    ("HI excitation ten times", "L[7] = ne * 7.5e-19", "L[7] = ne * 7.5e-18"),
+    ("HI excitation energy", "exp(-118348.0 / T)", "exp(-183480.0 / T)"),
+    ("HeII excitation power sign", "5.54e-17 * pow(T, -0.397)", "5.54e-17 * pow(T, 0.397)"),
+    ("free-free HeIII charge", "(nHII + nHeII + 4.0 * nHeIII)", "(nHII + nHeII + 2.0 * nHeIII)"),
+    ("free-free coefficient", "L[9] = 1.42e-27", "L[9] = 1.42e-26"),
+    ("HeI ionisation energy in cooling", "L[1] = ne * r[4] * nHeI * KB * T_HEI;", "L[1] = ne * r[4] * nHeI * KB * T_HI;"),
 ]
 
 # fast pins first; a mutant is killed at the first failure
 PINS = [
+    RT.test_case_b_hii_against_table,
+    RT.test_radiative_heii_recombination_against_table,
+    RT.test_heiii_recombination_is_hydrogenic,
+    RT.test_collisional_ionisation_against_independent_fit,
+    RT.test_collisional_ionisation_cooling_is_the_ionisation_energy,
+    RT.test_recombination_cooling_energy_per_recombination,
+    RT.test_dielectronic_recombination_energy_and_threshold,
+    RT.test_collisional_excitation_threshold_and_strength,
+    RT.test_free_free_coefficient_gaunt_and_charge,
     lambda: HP.test_roundtrip(2),
     lambda: HP.test_ring_latitudes_and_sizes(2),
     lambda: HP.test_children_nest_inside_parent(1),
