@@ -316,7 +316,13 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
             }
             int nb[3] = {cell[0], cell[1], cell[2]};
             nb[nax] += nside;
-            if (dmin < 0.5 * lpix && nb[nax] >= 0 && nb[nax] < n) {
+            if (p->geo_corr >= 2 && dmin < 0.5 * lpix) {
+                /* Sec. 3.6 variants: the primary factor alone (linear, or squared
+                 * as in the method it modifies); the rest of the absorbed photons
+                 * is credited to no cell */
+                fc = 0.5 + dmin / lpix;
+                if (p->geo_corr == 3) fc = fc * fc;
+            } else if (dmin < 0.5 * lpix && nb[nax] >= 0 && nb[nax] < n) {
                 fc = 0.5 + dmin / lpix;
                 nidx = ((int64_t)nb[0] * n + nb[1]) * n + nb[2];
                 double nns[3];
@@ -341,6 +347,8 @@ static void trace_ray(tctx* c, int level, uint64_t pix, double r0, const double*
                     /* a neighbour without absorbers of this group takes nothing */
                     deposit(c, idx, b, fc * A, kap[b]);
                     deposit(c, nidx, b, (1.0 - fc) * A, nkap[b]);
+                } else if (p->geo_corr >= 2) {
+                    deposit(c, idx, b, fc * A, kap[b]);
                 } else {
                     deposit(c, idx, b, A, kap[b]);
                 }

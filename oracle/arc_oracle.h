@@ -47,8 +47,11 @@ typedef struct {
     double alpha_B_fixed;          /* > 0: constant HII case-B coefficient          */
     int    coll_ion;               /* 1: collisional ionisation on                  */
     double z_compton;              /* >= 0: Compton cooling off the CMB at this z   */
-    int    geo_corr;               /* 1: geometric correction f_c with the secondary
-                                      f'_c to the nearest neighbour (Sec. 2.5)      */
+    int    geo_corr;               /* geometric correction (Sec. 2.5): 0 none; 1 f_c
+                                      with the secondary f'_c to the nearest
+                                      neighbour; 2 f_c alone; 3 f_c squared alone
+                                      (the last two are the Sec. 3.6 comparison
+                                      variants and do not conserve photons)       */
 } orc_params;
 
 /* end reasons of a ray */

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_chem as CH
+import test_oracle_correction as GC
 import test_oracle_healpix as HP
 import test_oracle_rates as RT
 import test_oracle_thin as TH
@@ -88,6 +89,8 @@ MUTANTS = [
     ("free-free HeIII charge", "(nHII + nHeII + 4.0 * nHeIII)", "(nHII + nHeII + 2.0 * nHeIII)"),
     ("free-free coefficient", "L[9] = 1.42e-27", "L[9] = 1.42e-26"),
     ("HeI ionisation energy in cooling", "L[1] = ne * r[4] * nHeI * KB * T_HEI;", "L[1] = ne * r[4] * nHeI * KB * T_HI;"),
+    # Sec. 3.6 correction variants
+    ("squared variant not squared", "if (p->geo_corr == 3) fc = fc * fc;", "if (p->geo_corr == 3) fc = fc;"),
 ]
 
 # fast pins first; a mutant is killed at the first failure
@@ -129,6 +132,7 @@ PINS = [
     TH.test_complementary_masks_add_up,
     lambda: TH.test_single_open_pixel_lights_its_cone(22),
     TH.test_thin_ledger_matches_the_cell_rates_with_helium,
+    GC.test_only_the_secondary_variant_conserves_photons,
 ]
 
 
