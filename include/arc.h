@@ -55,7 +55,7 @@ typedef struct arc_ctx arc_ctx;
 
 /* Uniform cubic grid of n^3 cells and physical side box_cm (Sec. 2.3). */
 typedef struct {
-    int n;               /* cells per side, 1 .. 4096                              */
+    int n;               /* cells per side, 1 .. 1280 (32-bit cell-record index)    */
     double box_cm;       /* side length [cm]                                        */
 } arc_grid;
 
@@ -169,7 +169,8 @@ arc_status arc_set_fields(arc_ctx* ctx, const float* nH, const float* xHI, const
  *   pos   nsrc*3 host doubles, grid units, inside [0,n)^3
  *   ndot  nsrc*ngroups host doubles, photons/s emitted in each group
  * Each source emits 12*4^l_base rays sharing its output equally (Sec. 2.4).
- * Positions are rounded to FP32 on the device; sources with no emission are
+ * Positions are kept on the device as FP32 pairs (hi + lo, ~1e-12 cell), so
+ * rays start from the caller's FP64 position; sources with no emission are
  * kept but trace no rays.  Returns ARC_E_INVALID for a position outside the
  * box or a negative/NaN rate.
  */

@@ -144,7 +144,7 @@ double yfrac(const arc_params& p) { return p.Y / (4.0 * (1.0 - p.Y)); }
 
 arc_status check_params(arc_ctx* c, const arc_grid* g, const arc_params* p) {
     if (!g || !p) return fail(c, ARC_E_INVALID, "null grid or params");
-    if (g->n < 1 || g->n > 4096) return fail(c, ARC_E_INVALID, "n=%d outside 1..4096", g->n);
+    if (g->n < 1 || g->n > ARC_MAX_N) return fail(c, ARC_E_INVALID, "n=%d outside 1..%d", g->n, ARC_MAX_N);
     if (!(g->box_cm > 0) || !isfinite(g->box_cm)) return fail(c, ARC_E_INVALID, "box_cm must be > 0");
     if (p->ngroups < 1 || p->ngroups > ARC_MAX_GROUPS)
         return fail(c, ARC_E_INVALID, "ngroups=%d outside 1..%d", p->ngroups, ARC_MAX_GROUPS);
@@ -231,12 +231,17 @@ arc_status upload_sources(arc_ctx* c) {
             tot += (double)N0[b];
         }
         emitted += s.total;
-        h[i].pos_thr = make_float4((float)s.pos[0], (float)s.pos[1], (float)s.pos[2],
-                                   (float)(c->p.term_frac * tot));
+        float ph[3], pl[3];
+        for (int a = 0; a < 3; ++a) {   // the FP64 position as an FP32 pair
+            ph[a] = (float)s.pos[a];
+            pl[a] = (float)(s.pos[a] - (double)ph[a]);
+        }
+        h[i].pos_thr = make_float4(ph[0], ph[1], ph[2], (float)(c->p.term_frac * tot));
         h[i].N0 = make_float4(N0[0], N0[1], N0[2], N0[3]);
+        h[i].pos_lo = make_float4(pl[0], pl[1], pl[2],
+                                  N0[0] > 0.f ? (float)((double)N0[0] * exp(-0.1)) : 0.f);   // Sec. 2.6
         h[i].id = s.id;
-        h[i].cthr0 = N0[0] > 0.f ? (float)((double)N0[0] * exp(-0.1)) : 0.f;   // Sec. 2.6
-        h[i].pad[0] = h[i].pad[1] = 0;
+        h[i].pad[0] = h[i].pad[1] = h[i].pad[2] = 0;
         c->dev_ids[i] = s.id;
     }
     const int ns = (int)act.size();
@@ -304,6 +309,8 @@ TraceArgs trace_args(arc_ctx* c) {
     memset(&a, 0, sizeof a);
     a.n = c->n;
     a.nb = c->nb;
+    a.bstride_y = (uint32_t)c->nb << 9;
+    a.bstride_x = a.bstride_y * (uint32_t)c->nb;
     a.ng = c->p.ngroups;
     a.l_base = c->p.l_base;
     a.l_max = c->p.l_max;

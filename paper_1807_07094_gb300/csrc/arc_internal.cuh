@@ -72,18 +72,26 @@ __host__ __device__ __forceinline__ int key_level(uint64_t key) { return (int)((
 __host__ __device__ __forceinline__ int key_k(uint64_t key) { return (int)((key >> 56) & 0x7); }
 
 // Per-source record on the device (sources sorted by luminosity, brightest first).
+// The position is an unevaluated pair per axis, hi + lo: the caller's FP64
+// value to ~1e-12 cell (hi alone would move the source by up to 3e-5 cell at
+// 512 cells, which changes the photons sent through optically thick cells by
+// ~1e-4).
 struct __align__(16) SourceDev {
-    float4 pos_thr;   // x, y, z [cells], photon threshold of one l_base ray [PHOT_UNIT]
+    float4 pos_thr;   // x, y, z [cells] (high parts), photon threshold of one l_base ray [PHOT_UNIT]
     float4 N0;        // photons of one l_base ray per group [PHOT_UNIT]
+    float4 pos_lo;    // x, y, z low parts [cells]; w: group-0 photons of one l_base ray after
+                      // optical depth 0.1 (N0.x exp(-0.1)), the optically thin radius test (Sec. 2.6)
     uint32_t id;      // index in the order the caller added the sources
-    float cthr0;      // group-0 photons of one l_base ray after optical depth 0.1
-                      // (N0.x exp(-0.1)), the optically thin radius test (Sec. 2.6)
-    uint32_t pad[2];
+    uint32_t pad[3];
 };
+static_assert(sizeof(SourceDev) == 64, "source record: two 32-byte sectors");
+// Brick-cell indices are 32-bit: n <= ARC_MAX_N keeps ceil(n/8)^3 * 512 below 2^32.
+#define ARC_MAX_N 1280
 
 // Arguments of the tracer kernels.
 struct TraceArgs {
     int n, nb, ng, l_base, l_max;
+    uint32_t bstride_x, bstride_y;     // record-index step of one brick along x (512 nb^2) and y (512 nb)
     // cell records [2 * brick cells]: [2q] optical depth per cell length per
     // group, [2q + 1] photons absorbed per group (FP32 sums); kappa and acc
     // both point at the record array

@@ -148,12 +148,16 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
             tot += (double)N0[b];
         }
         emitted += total[i];
-        hsrc[k].pos_thr = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2],
-                                      (float)(p->term_frac * tot));
+        float ph[3], pl[3];
+        for (int a = 0; a < 3; ++a) {   // the FP64 position as an FP32 pair
+            ph[a] = (float)pos[3 * i + a];
+            pl[a] = (float)(pos[3 * i + a] - (double)ph[a]);
+        }
+        hsrc[k].pos_thr = make_float4(ph[0], ph[1], ph[2], (float)(p->term_frac * tot));
         hsrc[k].N0 = make_float4(N0[0], N0[1], N0[2], N0[3]);
+        hsrc[k].pos_lo = make_float4(pl[0], pl[1], pl[2], 0.f);   // no optically thin radius on this path
         hsrc[k].id = (uint32_t)i;
-        hsrc[k].cthr0 = 0.f;   // no optically thin radius on this path
-        hsrc[k].pad[0] = hsrc[k].pad[1] = 0;
+        hsrc[k].pad[0] = hsrc[k].pad[1] = hsrc[k].pad[2] = 0;
     }
     const int per_src = 3 << (2 * p->l_base);
     const int nseeds = ns * per_src;
@@ -191,6 +195,8 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     memset(&A, 0, sizeof A);
     A.n = n;
     A.nb = nb;
+    A.bstride_y = (uint32_t)nb << 9;
+    A.bstride_x = A.bstride_y * (uint32_t)nb;
     A.ng = G;
     A.l_base = p->l_base;
     A.l_max = p->l_max;

@@ -31,7 +31,11 @@
 //   addition (TwoSum on the value the atomic returns) goes to an FP64 ledger;
 // * a cell's record is one 32-byte sector: its optical depth per cell length
 //   (read) followed by its absorbed photons (atomically added), so the read
-//   brings into L2 the sector the atomic then updates.
+//   brings into L2 the sector the atomic then updates;
+// * geometry per segment is one FP32-pair addition: the distance to the next
+//   plane of each axis is carried as a pair and advanced by |1/u| when that
+//   plane is crossed, and the record index steps in the brick/Morton layout
+//   (no per-segment recomputation from the source position).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -103,33 +107,33 @@ __device__ __forceinline__ float two_sum_err(float a, float b) {
 //   thin (a < 1/2): d = fl(Nh a), the ray subtracts d exactly;
 //   thick:          the survivors fl(Nh e^-tau) are formed directly (no
 //                   cancellation) and d + e is the exact difference.
-__device__ __forceinline__ float absorbed_fraction(float tau) {
-    // 1 - e^-tau.  Below tau = 3/4 (which covers the thin branch, tau < ln 2)
-    // the degree-11 Taylor polynomial: relative truncation error below
-    // tau^11 / 12! < 8e-11, Horner rounding ~1e-7, so the per-segment error
-    // does not build up along rays that cross many cells of moderate depth
-    // (a hardware exponential's ~2e-6 did: 1e-4 after ~50 such cells).  Above,
-    // the accurate exponential (only the branch test uses it there).  Photon
-    // conservation does not depend on it: the ray loses exactly what the cell
-    // receives.
-    if (tau < 0.75f) {
-        float q = 1.0f - tau * (1.0f / 11.0f);
-        q = 1.0f - tau * (1.0f / 10.0f) * q;
-        q = 1.0f - tau * (1.0f / 9.0f) * q;
-        q = 1.0f - tau * (1.0f / 8.0f) * q;
-        q = 1.0f - tau * (1.0f / 7.0f) * q;
-        q = 1.0f - tau * (1.0f / 6.0f) * q;
-        q = 1.0f - tau * (1.0f / 5.0f) * q;
-        q = 1.0f - tau * 0.25f * q;
-        q = 1.0f - tau * (1.0f / 3.0f) * q;
-        q = 1.0f - tau * 0.5f * q;
-        return tau * q;
-    }
-    return -expm1f(-tau);
+//
+// 1 - e^-tau for tau < ln 2 (the thin branch below): tau times the Taylor
+// series of (1 - e^-tau) / tau to degree 9, by Horner in x = -tau with one FMA
+// per term.  Truncation below tau^10 / 11! < 7e-10 relative, Horner rounding
+// ~1e-7, so the per-segment error does not build up along rays that cross many
+// cells of moderate depth (a hardware exponential's ~2e-6 did: 1e-4 after ~50
+// such cells).  Photon conservation does not depend on it: the ray loses
+// exactly what the cell receives.
+__device__ __forceinline__ float thin_fraction(float tau) {
+    const float x = -tau;
+    float q = 1.0f / 3628800.0f;
+    q = fmaf(q, x, 1.0f / 362880.0f);
+    q = fmaf(q, x, 1.0f / 40320.0f);
+    q = fmaf(q, x, 1.0f / 5040.0f);
+    q = fmaf(q, x, 1.0f / 720.0f);
+    q = fmaf(q, x, 1.0f / 120.0f);
+    q = fmaf(q, x, 1.0f / 24.0f);
+    q = fmaf(q, x, 1.0f / 6.0f);
+    q = fmaf(q, x, 0.5f);
+    q = fmaf(q, x, 1.0f);
+    return tau * q;
 }
+// The branch is chosen on tau itself (a < 1/2 exactly when tau < ln 2), so a
+// thick segment evaluates one exponential and a thin one none.
 __device__ __forceinline__ void absorb(float& Nh, float& Nl, float tau, float& d, float& e) {
-    const float a = absorbed_fraction(tau);
-    if (a < 0.5f) {
+    if (tau < 0.69314718f) {
+        const float a = thin_fraction(tau);
         d = __fmul_rn(Nh, a);
         e = 0.0f;
         const float s = __fsub_rn(Nh, d);                 // TwoSum(Nh, -d) = (s, r)
@@ -313,12 +317,12 @@ __device__ __forceinline__ void inv_pair(F2 u, float& ih, float& il) {
     il = (u.h == 0.0f) ? 0.0f : __fmul_rn(fmaf(-u.l, ih, fmaf(-u.h, ih, 1.0f)), ih);
 }
 
-// floor(o + r u) for the start cell, with u a pair: the sum is formed as a
-// pair and the floor taken of its exact value
-__device__ __forceinline__ int start_cell(float o, float r, F2 u) {
+// floor(o + r u) for the start cell, with the origin o = oh + ol and u pairs:
+// the sum is formed as a pair and the floor taken of its exact value
+__device__ __forceinline__ int start_cell(float oh, float ol, float r, F2 u) {
     const F2 p = f2_mul(F2{r, 0.0f}, u);
-    const float sh = __fadd_rn(o, p.h);
-    const float low = __fadd_rn(two_sum_err(o, p.h), p.l);
+    const float sh = __fadd_rn(oh, p.h);
+    const float low = __fadd_rn(__fadd_rn(two_sum_err(oh, p.h), p.l), ol);
     float c = floorf(sh);
     if (sh == c && low < 0.0f) c -= 1.0f;
     else if (low > 0.0f && low >= __fsub_rn(c + 1.0f, sh)) c += 1.0f;
@@ -430,42 +434,51 @@ __device__ int q_pop_warp(const TraceArgs& A, Entry& e, int want, int lane) {
 // EV_BLOCK: an emitted ray whose direction the source's mask blocks (Sec. 2.2)
 enum : int { EV_NONE = 0, EV_SPLIT = 1, EV_ESC = 2, EV_TERM = 3, EV_BLOCK = 4 };
 
-// Distances along the ray are unevaluated FP32 pairs (hi + lo, ~2^-44
-// relative): with plain FP32 a crossing distance t is off by ~t 2^-24 cells,
-// and behind cells of tens of optical depths that moves ~1e-4 of the photons.
+// Ray geometry (Sec. 2.4: the ray crosses the grid cell by cell).  The
+// distance from the source to the next X, Y and Z plane is carried as an
+// unevaluated FP32 pair (~2^-44 relative) and advanced by |1/u| (a pair as
+// well) when that plane is crossed: one pair addition per segment instead of
+// three plane-distance products.  With plain FP32 a crossing distance t would
+// be off by ~t 2^-24 cells, and behind cells of tens of optical depths that
+// moves ~1e-4 of the photons.  The ray's source, level and pixel are needed
+// only at events; they live in shared memory, one slot per thread, which keeps
+// them out of the registers of the segment loop.
 struct Ray {
-    float ox, oy, oz;      // source position [cells]
+    float tx, tlx, ty, tly, tz, tlz;   // next plane per axis (hi, lo); u = 0: hi = +inf and lo
+                                        // holds the fixed in-cell coordinate o - c
     float ix, iy, iz;      // 1/u per axis (+-inf for u = 0), high parts
     float ilx, ily, ilz;   // low parts of 1/u
-    int cx, cy, cz;        // current cell (the distances to its faces are
-                           // recomputed each segment rather than carried)
+    int cx, cy, cz;        // current cell
     float r, rl;           // distance travelled (hi + lo)
     float rstop, thr;
     float4 N;              // photons per group (high part)
     float4 Nl;             // low part: the photons are N + Nl
     float4 kap;            // optical depth per cell length of the current cell
-    uint64_t idx;          // internal index of the current cell
-    uint64_t pix;
-    uint32_t src;
-    int level;
+    uint32_t idx;          // brick-cell index of the current cell
     uint32_t visits;
     float cthr;            // thin radius: group-0 photons at optical depth 0.1 of this
                            // ray's share; 0 once reached (or the group is empty)
 };
+struct RayId {
+    uint64_t pix;
+    uint32_t src;
+    int level;
+};
+__shared__ RayId s_id[256];   // per thread of the block (k_trace blocks have <= 256 threads)
 
-// distance to the next plane on one axis as a pair th + tl:
-// (P - o)(ih + il) with P - o = ah + al exactly (TwoSum) and the product's
+// distance to the next plane on one axis from the origin oh + ol, as a pair
+// th + tl: (P - oh - ol)(ih + il) with P - oh exact (TwoSum) and the product's
 // rounding error recovered by FMA.  u > 0 (ih > 0): plane c + 1; u < 0: plane
 // c; u = 0 (ih infinite): +inf
-__device__ __forceinline__ float next_plane_t(int c, float o, float ih, float il, float& tl) {
+__device__ __forceinline__ float next_plane_t(int c, float oh, float ol, float ih, float il, float& tl) {
     const float P = (float)(c + (ih > 0.0f ? 1 : 0));
-    const float ah = __fsub_rn(P, o);
-    const float al = two_sum_err(P, -o);
+    const float ah = __fsub_rn(P, oh);
+    const float al = __fsub_rn(two_sum_err(P, -oh), ol);
     const float th = __fmul_rn(ah, ih);
-    tl = fmaf(al, ih, fmaf(ah, il, fmaf(ah, ih, -th)));
+    const F2 t = fast_two_sum(th, fmaf(al, ih, fmaf(ah, il, fmaf(ah, ih, -th))));
     const bool par = fabsf(ih) == INFINITY;
-    if (par) tl = 0.0f;
-    return par ? INFINITY : th;
+    tl = par ? 0.0f : t.l;
+    return par ? INFINITY : t.h;
 }
 
 // Start child k of entry e in this lane.  Returns EV_ESC if the child starts
@@ -476,9 +489,12 @@ __device__ __forceinline__ float next_plane_t(int c, float o, float ih, float il
 // launched at the thin radius): it splits at once without tracing a cell.
 template <bool EXT>
 __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int k, Ray& R) {
-    R.level = key_level(e.key);
-    R.pix = key_pixbase(e.key) + (uint64_t)k;
-    R.src = e.src;
+    const int level = key_level(e.key);
+    const uint64_t pix = key_pixbase(e.key) + (uint64_t)k;
+    RayId& id = s_id[threadIdx.x];
+    id.pix = pix;
+    id.src = e.src;
+    id.level = level;
     R.r = e.r;
     R.rl = 0.0f;
     R.N = e.N;
@@ -486,32 +502,37 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
     R.visits = 0;
     const SourceDev* S = &A.src[e.src];
     const float4 pt = __ldg(&S->pos_thr);
-    R.ox = pt.x;
-    R.oy = pt.y;
-    R.oz = pt.z;
-    R.thr = ldexpf(pt.w, -2 * (R.level - A.l_base));
-    R.rstop = (R.level < A.l_max) ? A.rsplit[R.level] : INFINITY;
+    const float4 pl = __ldg(&S->pos_lo);
+    R.thr = ldexpf(pt.w, -2 * (level - A.l_base));
+    R.rstop = (level < A.l_max) ? A.rsplit[level] : INFINITY;
     if (EXT) {
-        const float c = ldexpf(__ldg(&S->cthr0), -2 * (R.level - A.l_base));
+        const float c = ldexpf(pl.w, -2 * (level - A.l_base));
         R.cthr = (A.rnext != nullptr && R.N.x > c) ? c : 0.0f;
-        if (A.open != nullptr && R.level == A.l_base && A.open[(size_t)R.src * A.nbase + R.pix] == 0) {
+        if (A.open != nullptr && level == A.l_base && A.open[(size_t)e.src * A.nbase + pix] == 0) {
             R.cthr = 0.0f;
             return EV_BLOCK;
         }
     }
     F2 u[3];
-    healpix_dir(R.level, R.pix, u);
+    healpix_dir(level, pix, u);
     inv_pair(u[0], R.ix, R.ilx);
     inv_pair(u[1], R.iy, R.ily);
     inv_pair(u[2], R.iz, R.ilz);
-    R.cx = start_cell(R.ox, R.r, u[0]);
-    R.cy = start_cell(R.oy, R.r, u[1]);
-    R.cz = start_cell(R.oz, R.r, u[2]);
+    R.cx = start_cell(pt.x, pl.x, R.r, u[0]);
+    R.cy = start_cell(pt.y, pl.y, R.r, u[1]);
+    R.cz = start_cell(pt.z, pl.z, R.r, u[2]);
     const int n = A.n;
     if (R.cx < 0 || R.cx >= n || R.cy < 0 || R.cy >= n || R.cz < 0 || R.cz >= n) return EV_ESC;
+    float tl;
+    R.tx = next_plane_t(R.cx, pt.x, pl.x, R.ix, R.ilx, tl);
+    R.tlx = (R.tx == INFINITY) ? __fadd_rn(__fsub_rn(pt.x, (float)R.cx), pl.x) : tl;
+    R.ty = next_plane_t(R.cy, pt.y, pl.y, R.iy, R.ily, tl);
+    R.tly = (R.ty == INFINITY) ? __fadd_rn(__fsub_rn(pt.y, (float)R.cy), pl.y) : tl;
+    R.tz = next_plane_t(R.cz, pt.z, pl.z, R.iz, R.ilz, tl);
+    R.tlz = (R.tz == INFINITY) ? __fadd_rn(__fsub_rn(pt.z, (float)R.cz), pl.z) : tl;
     if (EXT && R.r >= R.rstop) return EV_SPLIT;
-    R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
-    R.kap = ldg_f4(&A.kappa[2 * R.idx]);
+    R.idx = (uint32_t)brick_index(R.cx, R.cy, R.cz, A.nb);
+    R.kap = ldg_f4(&A.kappa[2 * (size_t)R.idx]);
     return EV_NONE;
 }
 
@@ -522,20 +543,16 @@ __device__ __forceinline__ int start_ray(const TraceArgs& A, const Entry& e, int
 template <int NG, bool REC, bool EXT>
 __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) {
     // nearest plane; ties go to the lowest axis (x, y, z), as in the step below
-    float tlx, tly, tlz;
-    const float tx = next_plane_t(R.cx, R.ox, R.ix, R.ilx, tlx);
-    const float ty = next_plane_t(R.cy, R.oy, R.iy, R.ily, tly);
-    const float tz = next_plane_t(R.cz, R.oz, R.iz, R.ilz, tlz);
-    const bool ax = tx <= ty && tx <= tz;
-    const bool ay = !ax && ty <= tz;
-    const float t = ax ? tx : (ay ? ty : tz);
-    const float tl = ax ? tlx : (ay ? tly : tlz);
+    const bool ax = R.tx <= R.ty && R.tx <= R.tz;
+    const bool ay = !ax && R.ty <= R.tz;
+    const float t = ax ? R.tx : (ay ? R.ty : R.tz);
+    const float tl = ax ? R.tlx : (ay ? R.tly : R.tlz);
     // split where r_split <= t exactly (r_split is an FP32 value, t = hi + lo)
     const bool split = R.rstop < t || (R.rstop == t && tl >= 0.0f);
     const float r1 = split ? R.rstop : t;
     const float r1l = split ? 0.0f : tl;
     const float ds = fmaxf(__fadd_rn(__fsub_rn(r1, R.r), __fsub_rn(r1l, R.rl)), 0.0f);
-    const uint64_t idx = R.idx;
+    const uint32_t idx = R.idx;
     const float4 kap = R.kap;
     const float4 Nh0 = R.N, Nl0 = R.Nl;
     float4 D = make_float4(0.f, 0.f, 0.f, 0.f), E = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -548,7 +565,7 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
         // inside this segment, at r + ln(N_in / N_0.1) / kappa_0
         float ts = r1;
         if (kap.x > 0.0f) ts = fminf(fmaxf(R.r + logf(Nh0.x / R.cthr) / kap.x, R.r), r1);
-        atomicMin(reinterpret_cast<int*>(A.rnext) + R.src, __float_as_int(ts));
+        atomicMin(reinterpret_cast<int*>(A.rnext) + s_id[threadIdx.x].src, __float_as_int(ts));
         R.cthr = 0.0f;
     }
     float sumN = R.N.x;
@@ -570,14 +587,32 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
     // goes to the neighbour across that face (Eq. correction2, as photons split
     // over the neighbour's own absorbers in k_finalize).  The moved part is
     // taken from the absorbed part only; at a termination the residual stays.
-    uint64_t nidx = 0;
+    uint32_t nidx = 0;
     float4 Dn = make_float4(0.f, 0.f, 0.f, 0.f);
     bool corr = false;
     if (A.geo_corr && ds > 0.0f) {
-        const float rm = 0.5f * (R.r + r1);
-        const float ux = __frcp_rn(R.ix), uy = __frcp_rn(R.iy), uz = __frcp_rn(R.iz);   // 1/inf = 0
-        const float f[3] = {fmaf(rm, ux, R.ox) - (float)R.cx, fmaf(rm, uy, R.oy) - (float)R.cy,
-                            fmaf(rm, uz, R.oz) - (float)R.cz};
+        // in-cell coordinates of the midpoint from the pair distances: along an
+        // axis with u != 0 the far face (the next plane) lies (t_a - r_m)|u_a|
+        // away, to FP32 precision of that sub-cell distance; along u = 0 the
+        // coordinate is fixed
+        const F2 rm2 = f2_add(F2{R.r, R.rl}, F2{r1, r1l});
+        const float rm = 0.5f * rm2.h;
+        const F2 mrm = F2{-0.5f * rm2.h, -0.5f * rm2.l};
+        float f[3];
+        {
+            const float th[3] = {R.tx, R.ty, R.tz}, tlo[3] = {R.tlx, R.tly, R.tlz};
+            const float ih[3] = {R.ix, R.iy, R.iz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (th[a] == INFINITY) {
+                    f[a] = tlo[a];
+                } else {
+                    const F2 q = f2_add(F2{th[a], tlo[a]}, mrm);
+                    const float dn = __fdiv_rn(__fadd_rn(q.h, q.l), fabsf(ih[a]));
+                    f[a] = ih[a] > 0.0f ? __fsub_rn(1.0f, dn) : dn;
+                }
+            }
+        }
         float dmin = INFINITY;
         int nax = 0, nside = 0;
 #pragma unroll
@@ -586,13 +621,13 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
             if (1.0f - f[a] < dmin) { dmin = 1.0f - f[a]; nax = a; nside = 1; }
         }
         dmin = fmaxf(dmin, 0.0f);
-        const float lpix = rm * A.pixw[R.level];
+        const float lpix = rm * A.pixw[s_id[threadIdx.x].level];
         int nb[3] = {R.cx, R.cy, R.cz};
         nb[nax] += nside;
         if (dmin < 0.5f * lpix && nb[nax] >= 0 && nb[nax] < A.n) {
-            const float fc = 0.5f + __fdividef(dmin, lpix);
-            nidx = brick_index(nb[0], nb[1], nb[2], A.nb);
-            const float4 nk = ldg_f4(&A.kappa[2 * nidx]);
+            const float fc = 0.5f + __fdiv_rn(dmin, lpix);
+            nidx = (uint32_t)brick_index(nb[0], nb[1], nb[2], A.nb);
+            const float4 nk = ldg_f4(&A.kappa[2 * (size_t)nidx]);
             // moved photons per group (none where the neighbour has no absorber);
             // d - moved is exact because moved <= d / 2
             const float g = 1.0f - fc;
@@ -607,24 +642,40 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
     R.rl = r1l;
     int ev = term ? EV_TERM : (split ? EV_SPLIT : EV_NONE);
     if (ev == EV_NONE) {
-        // step across the nearest face; ties go to the lowest axis (x, y, z)
-        const int n = A.n;
-        bool out;
+        // step across the nearest face (ties to the lowest axis): the cell, that
+        // axis's next-plane distance (+ |1/u|) and the record index (that axis's
+        // Morton bits inside the 8^3 brick, carrying or borrowing into the brick
+        // index)
+        const float ih = ax ? R.ix : (ay ? R.iy : R.iz);
+        const float il = ax ? R.ilx : (ay ? R.ily : R.ilz);
+        const bool up = ih > 0.0f;
+        const F2 tn = f2_add(F2{t, tl}, F2{fabsf(ih), up ? il : -il});
+        const int c = (ax ? R.cx : (ay ? R.cy : R.cz)) + (up ? 1 : -1);
+        const uint32_t mk = ax ? 0x124u : (ay ? 0x92u : 0x49u);
+        const uint32_t bs = ax ? A.bstride_x : (ay ? A.bstride_y : 512u);
+        const uint32_t m = R.idx;
+        const uint32_t mm = up ? (((m | ~mk) + 1u) & mk) : (((m & mk) - 1u) & mk);
+        uint32_t ni = (m & ~mk) | mm;
+        if (up && mm == 0u) ni += bs;
+        if (!up && mm == mk) ni -= bs;
         if (ax) {
-            R.cx += (R.ix > 0.f) ? 1 : -1;
-            out = R.cx < 0 || R.cx >= n;
+            R.cx = c;
+            R.tx = tn.h;
+            R.tlx = tn.l;
         } else if (ay) {
-            R.cy += (R.iy > 0.f) ? 1 : -1;
-            out = R.cy < 0 || R.cy >= n;
+            R.cy = c;
+            R.ty = tn.h;
+            R.tly = tn.l;
         } else {
-            R.cz += (R.iz > 0.f) ? 1 : -1;
-            out = R.cz < 0 || R.cz >= n;
+            R.cz = c;
+            R.tz = tn.h;
+            R.tlz = tn.l;
         }
-        if (out) {
+        if ((unsigned)c >= (unsigned)A.n) {
             ev = EV_ESC;
         } else {
-            R.idx = brick_index(R.cx, R.cy, R.cz, A.nb);
-            R.kap = ldg_f4(&A.kappa[2 * R.idx]);
+            R.idx = ni;
+            R.kap = ldg_f4(&A.kappa[2 * (size_t)ni]);
         }
     }
     if (corr) {
@@ -863,11 +914,12 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                     const unsigned long long slot = base + __popc(evm & lt_mask);
                     if (slot < A.rec_cap) {
                         arc_ray_rec q;
-                        q.src = A.src[R.src].id;
-                        q.level = (uint8_t)R.level;
+                        const RayId& id = s_id[threadIdx.x];
+                        q.src = A.src[id.src].id;
+                        q.level = (uint8_t)id.level;
                         q.end = (uint8_t)ev;
                         q.pad = 0;
-                        q.pix = R.pix;
+                        q.pix = id.pix;
                         q.visits = R.visits;
                         q.r1 = R.r;
                         A.recs[slot] = q;
@@ -880,7 +932,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
             // Sec. 2.6: a ray that ends (escape, threshold) before its group-0
             // optical depth reaches 0.1 offers its whole length
             if (EXT && has_ev && !is_split && R.cthr > 0.0f)
-                atomicMin(reinterpret_cast<int*>(A.rnext) + R.src, __float_as_int(R.r));
+                atomicMin(reinterpret_cast<int*>(A.rnext) + s_id[threadIdx.x].src, __float_as_int(R.r));
             if (has_ev && !is_split) {
                 if (ev == EV_ESC) {
                     atomicAdd(&W.esc, ((double)R.N.x + (double)R.Nl.x) + ((double)R.N.y + (double)R.Nl.y) +
@@ -915,8 +967,9 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                 if (is_split) {
                     // children 1..3 wait on the deque; this lane continues with child 0
                     Entry e;
-                    e.key = make_key(R.pix << 2, R.level + 1, 1);
-                    e.src = R.src;
+                    const RayId id = s_id[threadIdx.x];
+                    e.key = make_key(id.pix << 2, id.level + 1, 1);
+                    e.src = id.src;
                     e.r = R.r;
                     e.N = make_float4(R.N.x * 0.25f, NG > 1 ? R.N.y * 0.25f : 0.f,
                                       NG > 2 ? R.N.z * 0.25f : 0.f, NG > 3 ? R.N.w * 0.25f : 0.f);
@@ -932,7 +985,7 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
                     if (NG > 3) fold_low(R.N.w, R.Nl.w, keep.w);
                 }
                 {
-                    const unsigned lv = __reduce_max_sync(FULL, is_split ? (unsigned)R.level : 0u);
+                    const unsigned lv = __reduce_max_sync(FULL, is_split ? (unsigned)s_id[threadIdx.x].level : 0u);
                     if (lane == 0) W.maxlev = max(W.maxlev, lv);
                 }
                 __syncwarp();

@@ -97,6 +97,22 @@ def test_ragged_grid_and_zero_sources():
     check_pair(w, xs)
 
 
+def test_fp64_source_positions_as_given():
+    """Source positions exactly as drawn in FP64 (no rounding to a grid the
+    FP32 tracer could hold exactly): the oracle gets the FP64 values, the GPU
+    the same values through arc_add_sources, which keeps them as FP32 pairs.
+    Trees and rates must match at the usual bars; a plain FP32 position (off by
+    up to ~4e-6 cell here) moves photons behind thick cells by more than 1e-4."""
+    w = W.cosmic(n=48, nsrc=8, sigma_ln=1.5, seed=21, quantise=False)
+    assert np.any(np.abs(w.src_pos - W.quantise_pos(w.src_pos)) > 1e-6)
+    assert np.any(w.src_pos.astype(np.float32).astype(np.float64) != w.src_pos)
+    xs = partly_ionised(w, seed=22, lo=-4, hi=0)
+    check_pair(w, xs)
+    w2 = W.thermal_128(n=32, box_kpc=6.6 * 32 / 128)
+    w2.src_pos = np.array([[0.5 + 1e-7 / 3, 0.5 + 2e-7 / 7, 0.5 - 3e-7 / 11]])
+    check_pair(w2, partly_ionised(w2, seed=23, lo=-5, hi=-1))
+
+
 def test_sources_on_cell_planes():
     """Sources exactly on cell vertices and at the box corner: rays whose
     direction has an exactly zero component then run inside a cell boundary
@@ -206,9 +222,9 @@ def test_geometric_correction_matches_oracle(seed):
     paper's 'nearest adjacent cell' is then undefined), which FP32 and FP64
     break differently; cells whose deposits depend on a choice closer than 4
     FP32 ulps of the largest distance (2n cells) are left out.  f_c itself
-    depends on D_edge / L_pix, D_edge from the FP32 midpoint (error up to ~4
-    ulps of 2n cells, 3e-5) and L_pix down to ~0.05 cells next to a source, so
-    the rates carry up to ~6e-4 relative error there: the bar is 1e-3."""
+    depends on D_edge / L_pix; the tracer forms the midpoint's in-cell
+    coordinates from its pair distances to the cell's faces, so D_edge carries
+    only FP32 relative error and the rates meet the usual 1e-4 bar."""
     w = W.cosmic(n=48, nsrc=6, sigma_ln=1.5, seed=seed)
     xs = partly_ionised(w, seed=seed + 10, lo=-4, hi=0)
     p = dict(w.params(), geo_corr=1)
@@ -231,7 +247,7 @@ def test_geometric_correction_matches_oracle(seed):
             ref = o[name][s]
             m = keep & (ref > 1e-6 * ref.max())
             rel = np.abs(g[name][s][m] - ref[m]) / ref[m]
-            assert rel.max() <= 1e-3, (name, s, float(rel.max()), int(m.sum()))
+            assert rel.max() <= GAMMA_RTOL, (name, s, float(rel.max()), int(m.sum()))
 
 
 def test_clump_test3_geometry():

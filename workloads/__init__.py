@@ -233,27 +233,30 @@ def cosmic_field(n: int, sigma_ln: float, mean_nH: float, seed: int) -> np.ndarr
 
 
 def place_sources(nH: np.ndarray, nsrc: int, ndot_lo: float, ndot_hi: float,
-                  frac: np.ndarray, seed: int):
+                  frac: np.ndarray, seed: int, quantise: bool = True):
     """Sources in cells drawn ~ nH^2 (with replacement), jittered by U(-0.4,0.4)
-    cells, positions quantised to 2^-12; luminosities log-uniform."""
+    cells, positions quantised to 2^-12 (or left as drawn, FP64, with
+    quantise=False); luminosities log-uniform."""
     rng = np.random.Generator(np.random.PCG64(seed + 7919))
     w = nH.astype(np.float64).ravel() ** 2
     w /= w.sum()
     cells = rng.choice(w.size, size=nsrc, replace=True, p=w)
     n = nH.shape[0]
     ijk = np.stack(np.unravel_index(cells, (n, n, n)), axis=1).astype(np.float64)
-    pos = quantise_pos(ijk + 0.5 + rng.uniform(-0.4, 0.4, size=(nsrc, 3)))
+    pos = ijk + 0.5 + rng.uniform(-0.4, 0.4, size=(nsrc, 3))
+    if quantise:
+        pos = quantise_pos(pos)
     lum = 10.0 ** rng.uniform(math.log10(ndot_lo), math.log10(ndot_hi), size=nsrc)
     return pos, lum[:, None] * frac[None, :]
 
 
 def cosmic(n: int = 256, nsrc: int = 1000, sigma_ln: float = 1.5, seed: int = 1807,
            ndot_lo: float = 1e48, ndot_hi: float = 1e51, box_kpc: Optional[float] = None,
-           mean_nH: float = 2e-4) -> Workload:
+           mean_nH: float = 2e-4, quantise: bool = True) -> Workload:
     """Lognormal cosmic-field workload (stand-in for RT06 Test 4)."""
     grp = blackbody_groups(1e5)
     nH = cosmic_field(n, sigma_ln, mean_nH, seed)
-    pos, ndot = place_sources(nH, nsrc, ndot_lo, ndot_hi, grp["frac"], seed)
+    pos, ndot = place_sources(nH, nsrc, ndot_lo, ndot_hi, grp["frac"], seed, quantise)
     if box_kpc is None:
         # 0.5 h^-1 cMpc at z = 9 (h = 0.7) per 256 cells: same cell size at any n
         box_kpc = 500.0 / 0.7 / 10.0 * n / 256
