@@ -714,6 +714,24 @@ static int chem_subcycled(const orc_params* p, int64_t ncell, const double* nHa,
                 h = lim / fabs(dnHI);
                 last = 0;
             }
+            /* ... and of the helium densities n_HeI, n_HeII, n_HeIII (each
+             * floored at x_fp64 n_He): Sec. 2.7 limits the change of every
+             * quantity the equations track; the printed formula shows only the
+             * pure-hydrogen pair */
+            if (nHe > 0.0) {
+                const double nHeIII = nHe - nHeI - nHeII;
+                const double dHeI = r[1] * ne * nHeII - (G1 + r[4] * ne) * nHeI;
+                const double dHeIII = (G2 + r[5] * ne) * nHeII - r[2] * ne * nHeIII;
+                const double dHe[3] = {dHeI, -dHeI - dHeIII, dHeIII};
+                const double nHeS[3] = {nHeI, nHeII, nHeIII};
+                for (int k = 0; k < 3; k++) {
+                    const double limk = eps * fmax(nHeS[k], p->x_fp64 * nHe);
+                    if (fabs(dHe[k]) * h > limk) {
+                        h = limk / fabs(dHe[k]);
+                        last = 0;
+                    }
+                }
+            }
             double E = 0.0, Edot = 0.0;
             if (!p->isothermal) {
                 E = 1.5 * KB * T * (nH + nHe + ne);

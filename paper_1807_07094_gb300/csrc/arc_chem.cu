@@ -2,7 +2,8 @@
 //
 // Sec. 2.7 (Eq. diffeq in the D - C n form of Eq. anninos, backward
 // difference, sub-cycled between radiative-transfer steps with the step
-// limited to a fraction eps of the change of E, n_HI and n_HII) and Sec. 2.8
+// limited to a fraction eps of the change of E, n_HI, n_HII, n_HeI, n_HeII
+// and n_HeIII: every quantity the equations track) and Sec. 2.8
 // (photoheating minus cooling).  One thread per cell.
 //
 // The update is written per hydrogen atom: abundances a_s = n_s / n_H and
@@ -162,6 +163,23 @@ __global__ void __launch_bounds__(256) k_chem(const ChemArgs C) {
             if (fabsf(dHI) * h > lim) {
                 h = lim / fabsf(dHI);
                 last = false;
+            }
+            // ... and of HeI, HeII, HeIII (each floored at xfloor of the helium):
+            // the limit covers every quantity the equations track (Sec. 2.7)
+            if (y > 0.0f) {
+                const float a3 = y - a1 - a2;
+                const float d1 = r.a2 * nxe * a2 - (G1 + r.b1 * nxe) * a1;
+                const float d3 = (G2 + r.b2 * nxe) * a2 - r.a3 * nxe * a3;
+                const float dh[3] = {d1, -d1 - d3, d3};
+                const float ah[3] = {a1, a2, a3};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float limk = C.eps * fmaxf(ah[k], C.xfloor * y);
+                    if (fabsf(dh[k]) * h > limk) {
+                        h = limk / fabsf(dh[k]);
+                        last = false;
+                    }
+                }
             }
             float e = 0.0f, edot = 0.0f;
             if (!C.isothermal) {
