@@ -110,6 +110,24 @@ def test_training_fits_a_teacher():
     assert abs(l64 - last) <= 0.1 * last + 1e-4
 
 
+def test_package_trainer_fits_a_teacher():
+    """The package's training loop (paper_1807_07094_gb300.train: cosine AdamW
+    on the tensor-core trainer, He-normal start) learns a random teacher."""
+    from paper_1807_07094_gb300 import train as T
+    n = 2048
+    rng = np.random.Generator(np.random.PCG64(15))
+    teacher = _random_params(16, noise=0.0)
+    X = rng.normal(0, 1, (16 * n, 12))
+    Y, _ = M.forward(teacher, X)
+    Y = (Y - Y.mean(0)) / Y.std(0)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    Yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+    first, _ = M.loss_grad(T.init_params(17).astype(np.float64), X[:n], Y[:n])
+    learned, hist = T.train(Xd, Yd, epochs=40, batch=n, lr0=2e-3, wd=0.0, seed=17, log=lambda s: None)
+    last, _ = M.loss_grad(learned.astype(np.float64), X[:n], Y[:n])
+    assert len(hist) == 40 and first > 0.5 and last < first / 20, (first, last)
+
+
 def _chem_cells(params_dict, cells, dt, surrogate=None, tol_x=5e-4, tol_e=1e-2, gate=0.0):
     """arc_chem_update on a flat list of cells laid out as an n^3 grid."""
     nH, xHI, xHeI, xHeII, T, gamma, heat = cells

@@ -16,11 +16,12 @@ the hydrogen and energy changes per sub-step; its helium fractions carry a
 first-order error of up to ~1e-2, so they are no label to learn.)  Each
 labelled cell is one (state, rates, dt) -> (state') sample.
 
-Training runs on the GPU through the library's trainer (BF16 tensor-core
-forward/backward, FP32 AdamW): features and raw targets come from the
-library's own feature/target kernels, so that training sees exactly what
-inference computes.  This script is test infrastructure: it drives the
-oracle, which the library never does.
+Training runs on the GPU through the package's trainer
+(paper_1807_07094_gb300.train: BF16 tensor-core forward/backward, FP32
+AdamW, features and raw targets from the library's own kernels, so that
+training sees exactly what inference computes).  This script is test
+infrastructure: it drives the oracle to make the labels, which the library
+never does.
 """
 from __future__ import annotations
 
@@ -40,7 +41,6 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 DT0 = 0.02 * W.MYR
-OUT_S = np.array([1e-6, 1e-6, 1e-6, 1e-5])   # asinh scales of the 4 corrections
 
 
 def converged(p, nH, x0, T0, g, h, dt):
@@ -98,79 +98,6 @@ def gather(seeds, n, nsrc, nsteps, per_step, workers):
     return [st for s in seeds for st in out[s]]
 
 
-def device_samples(steps, params, stream):
-    """Features X [N, 12] and raw targets R [N, 4] (corrections to the physics
-    predictor) on the GPU via the library."""
-    import torch
-    import paper_1807_07094_gb300 as P
-    from paper_1807_07094_gb300 import arc
-    dev = torch.device("cuda")
-    Xs, Rs = [], []
-    with P.Arc(8, 1e21, params) as ctx:
-        for st in steps:
-            t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in st.items() if k != "dt"}
-            m = t["nH"].numel()
-            X = torch.empty((m, 12), dtype=torch.float32, device=dev)
-            R = torch.empty((m, 4), dtype=torch.float32, device=dev)
-            torch.cuda.synchronize()
-            arc.arc_mlp_features(t["nH"], t["x0"][0], t["x0"][1], t["x0"][2], t["T0"], t["gamma"], t["heat"],
-                                 st["dt"], X, stream)
-            ctx.mlp_targets(t["nH"], t["x0"], t["T0"], t["gamma"], t["heat"], t["x1"], t["T1"], st["dt"], R)
-            torch.cuda.synchronize()
-            Xs.append(X)
-            Rs.append(R)
-    return torch.cat(Xs), torch.cat(Rs)
-
-
-def fit_norm(X, R):
-    import torch
-    in_mu = X.double().mean(0)
-    in_sd = X.double().std(0).clamp_min(1e-3)
-    U = torch.asinh(R.double() / torch.tensor(OUT_S, dtype=torch.float64, device=R.device))
-    out_mu = U.mean(0)
-    out_sd = U.std(0).clamp_min(1e-3)
-    norm = torch.cat([in_mu, in_sd, out_mu, out_sd, torch.tensor(OUT_S, dtype=torch.float64, device=R.device)])
-    return norm.float().cpu().numpy()
-
-
-def normalise(X, R, norm):
-    import torch
-    q = torch.from_numpy(norm.astype(np.float64)).to(X.device)
-    Xn = ((X.double() - q[:12]) / q[12:24]).float()
-    Yn = ((torch.asinh(R.double() / q[32:36]) - q[24:28]) / q[28:32]).float()
-    return Xn.contiguous(), Yn.contiguous()
-
-
-def train(Xn, Yn, epochs, batch, lr0, wd, seed, stream, log=print):
-    import torch
-    from paper_1807_07094_gb300 import arc
-    import mlp_ref
-    N = Xn.shape[0] // batch * batch
-    tr = arc.MlpTrainer(batch, stream)
-    tr.set_params(mlp_ref.init_params(seed))
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    nb = N // batch
-    total = epochs * nb
-    k = 0
-    hist = []
-    for ep in range(epochs):
-        perm = torch.randperm(Xn.shape[0], generator=g)[:N].to(Xn.device)
-        Xp, Yp = Xn[perm].contiguous(), Yn[perm].contiguous()
-        acc = 0.0
-        for b in range(nb):
-            lr = lr0 * 0.5 * (1 + np.cos(np.pi * k / total)) + 1e-6
-            want = b % 50 == 0
-            loss = tr.step(Xp[b * batch:(b + 1) * batch], Yp[b * batch:(b + 1) * batch], batch, lr, wd, want)
-            if want:
-                acc = loss if acc == 0.0 else 0.8 * acc + 0.2 * loss
-            k += 1
-        hist.append(acc)
-        log(f"  epoch {ep}: loss {acc:.3e}")
-    P = tr.get_params()
-    tr.close()
-    return P, hist
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -190,23 +117,16 @@ def main():
     steps = gather(seeds, a.n, a.nsrc, a.nsteps, a.per_step, a.workers)
     t1 = time.time()
     print(f"oracle data: {len(steps)} steps in {t1 - t0:.0f} s", flush=True)
-    import torch
-    s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        X, R = device_samples(steps, W.cosmic(n=8, nsrc=1).params(), s.cuda_stream)
-        s.synchronize()
-        norm = fit_norm(X, R)
-        Xn, Yn = normalise(X, R, norm)
-        s.synchronize()
-        P, hist = train(Xn, Yn, a.epochs, a.batch, a.lr, a.wd, seeds[0], s.cuda_stream)
+    from paper_1807_07094_gb300 import train as T
+    P, norm, hist, nsamples = T.train_surrogate(steps, W.cosmic(n=8, nsrc=1).params(), a.epochs, a.batch,
+                                                a.lr, a.wd, seeds[0])
     t2 = time.time()
     meta = dict(recipe="FP64 oracle trajectories of lognormal cosmic fields (sigma_ln 1.5, P(k)~k^-3, mean nH 2e-4); "
                 "labels: converged update (Richardson of sub-step caps dt/200, dt/400)",
-                n=a.n, nsrc=a.nsrc, nsteps=a.nsteps, seeds=seeds, per_step=a.per_step, samples=int(X.shape[0]),
+                n=a.n, nsrc=a.nsrc, nsteps=a.nsteps, seeds=seeds, per_step=a.per_step, samples=nsamples,
                 epochs=a.epochs,
                 batch=a.batch, lr=a.lr, wd=a.wd, loss=hist, oracle_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))
-    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-    np.savez(a.out, params=P.astype(np.float32), norm=norm.astype(np.float32), meta=json.dumps(meta))
+    T.save_weights(a.out, P, norm, meta)
     print(json.dumps(meta))
 
 
