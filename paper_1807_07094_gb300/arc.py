@@ -513,7 +513,11 @@ class Arc:
         arc_clear_sources(self.ctx)
 
     def trace(self, dt: float = 1.0, budget: bool = True):
-        """Returns (gamma, heat) as zero-copy torch views [3,n,n,n] and the budget."""
+        """Returns (gamma, heat) as zero-copy torch views [3,n,n,n] and the budget.
+
+        The rates are written on the context's CUDA stream; with budget=False
+        the call does not wait for them, so synchronise that stream (or the
+        device) before reading the views from another stream."""
         g, h, b = arc_trace(self.ctx, dt, budget)
         sh = (3, self.n, self.n, self.n)
         return device_view(g, sh), device_view(h, sh), b
