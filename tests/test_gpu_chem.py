@@ -166,3 +166,63 @@ def test_clump_test3_against_printed_results():
     assert (Ta[(rL > 0.65) & (rL < 0.88)] < gold["T_inside_clump_below_K"]).all()
     assert (xa[rL > 0.9] > 0.5).all()
     assert (xa[(rL > 0.05) & (rL < 0.55)] < 1e-3).all()
+
+
+def _oracle_chem_chunk(args):
+    """One slice of cells through the FP64 oracle's chemistry (a spawned worker;
+    the inputs are memory-mapped FP32 arrays, so workers share one copy)."""
+    d, params, dt, lo, hi = args
+    import os
+    import oracle as O
+    ld = lambda name: np.load(os.path.join(d, name + ".npy"), mmap_mode="r")
+    s = slice(lo, hi)
+    f = lambda a: np.asarray(a, np.float64)
+    x0, g, h = ld("x0"), ld("g"), ld("h")
+    r = O.chem(params, f(ld("nH")[s]), f(x0[0, s]), f(x0[1, s]), f(x0[2, s]), f(ld("T0")[s]), f(g[:, s]),
+               f(h[:, s]), dt)
+    return lo, [np.asarray(a, np.float32) for a in r[:4]], int(r[5])
+
+
+def test_full_size_cosmic_256_chemistry_every_cell(tmp_path):
+    """The 256^3 benchmark field after three graph-replayed steps (fronts around
+    1000 sources, helium ionising next to the bright ones): one chemistry update
+    on the GPU against the oracle's on every one of the 16.7M cells, with the
+    rates the GPU traced.  The oracle runs in worker processes started with
+    spawn, one slice of cells each."""
+    import multiprocessing as mp
+    import os
+    w = W.cosmic_256()
+    with P.Arc(w.n, w.box_cm, w.params()) as a:
+        a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
+        a.add_sources(w.src_pos, w.src_ndot)
+        for _ in range(3):
+            a.step(w.dt_s)
+        state = a.get_fields()
+        g, h, _ = a.trace(w.dt_s, budget=True)          # budget=True waits for the rates
+        g = g.cpu().numpy().reshape(3, -1)
+        h = h.cpu().numpy().reshape(3, -1)
+        a.set_fields(w.nH, *state)
+        a.chem(w.dt_s)
+        st = a.stats()
+        out = a.get_fields()
+    assert st["chem_capped"] == 0 and st["chem_fp64_substeps"] > 0
+    f32 = lambda x: np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1))
+    d = str(tmp_path)
+    for name, arr in (("nH", f32(w.nH)), ("x0", np.stack([f32(s) for s in state[:3]])), ("T0", f32(state[3])),
+                      ("g", g.astype(np.float32)), ("h", h.astype(np.float32))):
+        np.save(os.path.join(d, name + ".npy"), arr)
+    n3 = w.n ** 3
+    step = n3 // 64
+    ox = [np.zeros(n3, np.float32) for _ in range(4)]
+    capped = 0
+    jobs = [(d, w.params(), w.dt_s, i, min(i + step, n3)) for i in range(0, n3, step)]
+    with mp.get_context("spawn").Pool(max(1, min(16, len(os.sched_getaffinity(0))))) as pool:
+        for lo, res, c in pool.imap_unordered(_oracle_chem_chunk, jobs):
+            for k in range(4):
+                ox[k][lo:lo + res[k].size] = res[k]
+            capped += c
+    f = lambda x: np.asarray(x, np.float64).reshape(-1)
+    assert capped == 0
+    for k in range(3):
+        assert np.max(np.abs(f(out[k]) - ox[k])) < X_ATOL, k
+    assert np.max(np.abs(f(out[3]) / ox[3] - 1)) < T_RTOL
