@@ -323,6 +323,7 @@ TraceArgs trace_args(arc_ctx* c) {
         a.pixw[l] = (float)sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * l)));   // Omega_l = 4 pi / (12 4^l)
     }
     a.geo_corr = c->p.geo_correction ? 1 : 0;
+    fill_sincos_table(a);
     a.open = c->hopen.empty() ? nullptr : c->dopen;
     a.nbase = 12 << (2 * c->p.l_base);
     a.rnext = c->p.thin_approx ? c->rnext : nullptr;

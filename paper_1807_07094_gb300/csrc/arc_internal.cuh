@@ -101,6 +101,9 @@ struct TraceArgs {
     int nsrc;
     float rsplit[ARC_MAX_LEVEL + 1];   // split distance per level [cells]
     float pixw[ARC_MAX_LEVEL + 1];     // pixel width per unit distance, sqrt(Omega_l)
+    // sin and cos of pi j / 64, j = -16..16, as FP32 pairs (sin hi, sin lo, cos hi,
+    // cos lo), formed once on the host in FP64 (fill_sincos_table)
+    float4 sincos[33];
     int geo_corr;                      // geometric correction (Sec. 2.5) on
     // anisotropic escape (Sec. 2.2): open[src * nbase + pix] == 0 blocks emitted
     // ray pix of device source src (nullptr: all open)
@@ -263,6 +266,8 @@ cudaError_t launch_mlp_targets(const ChemArgs& c, const float* x1, const float* 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_seed_reset(const TraceArgs& a, unsigned long long qcap, int nseeds, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s);
+// the HEALPix longitude table of TraceArgs (host)
+void fill_sincos_table(TraceArgs& a);
 cudaError_t launch_finalize(const FinalizeArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_budget(const double* part, int nparts, const double* escaped, const double* rounding,
                           const double* thin, double* out,

@@ -206,6 +206,7 @@ extern "C" arc_status arc_trace_noalloc(const arc_grid* g, const arc_params* p, 
     A.nsrc = ns;
     for (int l = 0; l <= ARC_MAX_LEVEL; ++l) A.rsplit[l] = (float)na_r_split(p->phi, l);
     A.seeds = seeds;
+    fill_sincos_table(A);
     A.nseeds = nseeds;
     A.seed_head = &scal->seed_head;
     A.qdata = qdata;

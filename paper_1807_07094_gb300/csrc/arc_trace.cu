@@ -223,15 +223,10 @@ __device__ __forceinline__ F2 f2_sqrt(F2 x) {
 }
 
 // sin and cos of pi j / 64, j = -16..16, as pairs (sin h, sin l, cos h, cos l):
-// each block of the tracer fills this table once from FP64 sincospi
+// each block of the tracer copies the table the host formed in FP64 (TraceArgs)
 __shared__ float4 s_sincos[33];
-__device__ __forceinline__ void fill_sincos_table() {
-    if (threadIdx.x < 33) {
-        double sd, cd;
-        sincospi((double)((int)threadIdx.x - 16) / 64.0, &sd, &cd);
-        const float sh = (float)sd, ch = (float)cd;
-        s_sincos[threadIdx.x] = make_float4(sh, (float)(sd - (double)sh), ch, (float)(cd - (double)ch));
-    }
+__device__ __forceinline__ void load_sincos_table(const TraceArgs& A) {
+    if (threadIdx.x < 33) s_sincos[threadIdx.x] = A.sincos[threadIdx.x];
     __syncthreads();
 }
 
@@ -700,7 +695,9 @@ struct WarpTally {
 };
 
 #ifndef ARC_SEG_BATCH
-#define ARC_SEG_BATCH 16   // measured on the 256^3 field: 4 -> 53.7, 8 -> 56.9, 16 -> 57.6 Gsegments/s
+#define ARC_SEG_BATCH 32   // measured on the 256^3 field, 1000 sources (this tracer, lane ledgers in
+                           // shared memory): 12 -> 54.2, 16 -> 58.2, 24 -> 61.0, 32 -> 61.6,
+                           // 48 -> 60.0, 64 -> 59.5 Gsegments/s
 #endif
 #ifndef ARC_REFILL_IDLE
 #define ARC_REFILL_IDLE 16
@@ -730,9 +727,14 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
     __shared__ WarpTally tally_all[8];
     WarpTally& W = tally_all[wib];
     if (lane == 0) W = WarpTally{};
-    fill_sincos_table();   // also orders the tallies' initialisation
-    unsigned nseg = 0;                 // per lane
-    double rounding = 0.0;             // photons the FP32 cell sums rounded away (exact)
+    load_sincos_table(A);   // also orders the tallies' initialisation
+    // per-lane segment count and rounding ledger (photons the FP32 cell sums
+    // rounded away, exact) in shared memory: updated once per batch, they hold
+    // no registers in the segment loop
+    __shared__ double s_round[256];
+    __shared__ unsigned s_nseg[256];
+    s_round[threadIdx.x] = 0.0;
+    s_nseg[threadIdx.x] = 0u;
     unsigned round = 0;
 
     Ray R;
@@ -892,13 +894,14 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
         // ------------------------------------------------------------ trace
         if (active && ev == EV_NONE) {
             float rerr = 0.0f;   // rounding ledger of this batch (a few ulps of its deposits)
+            int it = 0;
 #pragma unroll 1
-            for (int it = 0; it < SEG_BATCH; ++it) {
+            for (; it < SEG_BATCH; ++it) {
                 ev = segment<NG, REC, EXT>(A, R, rerr);
-                nseg++;
                 if (ev != EV_NONE) break;
             }
-            rounding += (double)rerr;
+            s_nseg[threadIdx.x] += (unsigned)(it < SEG_BATCH ? it + 1 : SEG_BATCH);
+            s_round[threadIdx.x] += (double)rerr;
         }
 
         // ------------------------------------------------------------ events
@@ -1018,7 +1021,8 @@ __global__ void __launch_bounds__(256, ARC_TRACE_MIN_BLOCKS) k_trace(const Trace
     flush_live();
     // per-lane counts stay far below 2^32 per launch; warp sums are formed in
     // the 64-bit atomics below, lane by lane
-    unsigned long long wseg = nseg;
+    unsigned long long wseg = s_nseg[threadIdx.x];
+    double rounding = s_round[threadIdx.x];
     for (int o = 16; o > 0; o >>= 1) {
         wseg += __shfl_down_sync(FULL, wseg, o);
         rounding += __shfl_down_sync(FULL, rounding, o);
@@ -1316,6 +1320,15 @@ void launch_trace_ng(const TraceArgs& a, int grid, int block, int smem, cudaStre
     else if (a.ng <= 3) k_trace<3, REC, EXT><<<grid, block, smem, s>>>(a);
     else k_trace<4, REC, EXT><<<grid, block, smem, s>>>(a);
 }
+void fill_sincos_table(TraceArgs& a) {
+    for (int j = -16; j <= 16; ++j) {
+        const double x = M_PI * (double)j / 64.0;
+        const double sd = sin(x), cd = cos(x);
+        const float sh = (float)sd, ch = (float)cd;
+        a.sincos[j + 16] = make_float4(sh, (float)(sd - (double)sh), ch, (float)(cd - (double)ch));
+    }
+}
+
 cudaError_t launch_trace(const TraceArgs& a, int grid, int block, cudaStream_t s) {
     const int smem = trace_smem_bytes(block, a.stack_log2);
     const bool ext = a.rnext != nullptr || a.open != nullptr;
