@@ -290,8 +290,13 @@ def cpu_leg(w, state, sample, gpu_sample, gpu_tree, chem_probe, max_workers: int
     ns = np.stack([w.nH * state[0], y * w.nH * state[1], y * w.nH * state[2]]).astype(np.float64)
     thr = p["term_frac"] * float(w.src_ndot[sample].sum(axis=1).max()) / 48.0
     absorbed = ns * V * g
-    errs_dec = {name: rate_errors(gpu_sample[name], ref, absorbers=absorbed / np.maximum(ref, 1e-300),
-                                  min_photons=1e4 * thr) for name, ref in (("gamma", g), ("heat", h))}
+
+    def per_rate(ref):          # absorbers per unit of the compared rate (0 where it vanishes)
+        out = np.zeros_like(absorbed)
+        np.divide(absorbed, ref, out=out, where=ref > 0)
+        return out
+    errs_dec = {name: rate_errors(gpu_sample[name], ref, absorbers=per_rate(ref), min_photons=1e4 * thr)
+                for name, ref in (("gamma", g), ("heat", h))}
     worst = lambda e: max(x[0] for x in e)
     over = lambda e: sum(x[2]["n_over_1e4"] if isinstance(x[2], dict) and "n_over_1e4" in x[2] else 0 for x in e)
     tree = None
