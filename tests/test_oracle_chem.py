@@ -251,3 +251,22 @@ def test_rt_timestep_single_cell_closed_form():
     one = [oracle.rt_timestep(p, [a], [b], [0.0], [0.0], [1e4], [G], eps) for a, b in zip(nH, x)]
     both = oracle.rt_timestep(p, nH, x, np.zeros(3), np.zeros(3), np.full(3, 1e4), np.full(3, G), eps)
     assert both == (min(o[0] for o in one), min(o[1] for o in one))
+
+
+@pytest.mark.parametrize("G1dt", [0.3, 1.0, 3.0])
+def test_helium_photoionisation_follows_the_exponential(G1dt):
+    """Neutral hydrogen (no HI rate), helium photoionised out of HeI at a
+    constant rate, isothermal, no collisional ionisation: with n_e ~ 1e-4 n_H
+    recombination is negligible over dt, so x_HeI(dt) = exp(-Gamma_HeI dt) and
+    x_HeII = 1 - x_HeI.  Sub-steps limited in every helium density (Sec. 2.7)
+    keep the backward-difference update within 3e-2 of it; a limit on n_HI and E
+    alone would take one step (x_HeI = 1 / (1 + Gamma dt), off by 0.13 at
+    Gamma dt = 1)."""
+    dt = 0.02 * W.MYR
+    p = params(Y=0.24, isothermal=1, coll_ion=0)
+    xHI, xHeI, xHeII, T, nsub, capped = run_cell(p, 1e-3, 1.0, 1.0, 0.0, 1e4, [0.0, G1dt / dt, 0.0],
+                                                 [0, 0, 0], dt)
+    assert capped == 0
+    exact = math.exp(-G1dt)
+    assert abs(xHeI[0] - exact) < 3e-2, (xHeI[0], exact)
+    assert abs(xHeII[0] - (1 - exact)) < 3e-2

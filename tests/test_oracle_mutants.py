@@ -89,6 +89,8 @@ MUTANTS = [
     ("free-free HeIII charge", "(nHII + nHeII + 4.0 * nHeIII)", "(nHII + nHeII + 2.0 * nHeIII)"),
     ("free-free coefficient", "L[9] = 1.42e-27", "L[9] = 1.42e-26"),
     ("HeI ionisation energy in cooling", "L[1] = ne * r[4] * nHeI * KB * T_HEI;", "L[1] = ne * r[4] * nHeI * KB * T_HI;"),
+    ("helium sub-step limit dropped", "            if (nHe > 0.0) {\n                const double nHeIII = nHe - nHeI - nHeII;",
+     "            if (0) {\n                const double nHeIII = nHe - nHeI - nHeII;"),
     # Sec. 3.6 correction variants
     ("squared variant not squared", "if (p->geo_corr == 3) fc = fc * fc;", "if (p->geo_corr == 3) fc = fc;"),
 ]
@@ -121,6 +123,7 @@ PINS = [
     CH.test_photoheating_of_neutral_gas_is_linear,
     CH.test_compton_coefficient,
     CH.test_collisional_ionisation_equilibrium,
+    lambda: CH.test_helium_photoionisation_follows_the_exponential(1.0),
     TR.test_termination_distance_in_uniform_medium,
     TR.test_rays_per_face_at_split_equals_phi,
     TR.test_optically_thin_shells,
