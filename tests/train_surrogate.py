@@ -98,6 +98,121 @@ def gather(seeds, n, nsrc, nsteps, per_step, workers):
     return [st for s in seeds for st in out[s]]
 
 
+def _label_chunk(args):
+    """Converged update of one chunk of sampled cells (a spawned worker)."""
+    p, nH, x0, T0, g, h, dt = args
+    xs, Ts = converged(p, nH.astype(np.float64), x0.astype(np.float64), T0.astype(np.float64),
+                       g.astype(np.float64), h.astype(np.float64), dt)
+    return np.stack([np.asarray(v, np.float32) for v in xs]), np.asarray(Ts, np.float32)
+
+
+def gpu_states(configs, nsteps, per_step, workers, seed0=7919):
+    """Cell samples of the C4 configurations: cosmic fields at 128^3 and 256^3
+    with the benchmark's cell size, density statistics and source density,
+    advanced on the GPU (trace + the paper's sub-cycled chemistry, both matched
+    to the oracle by the parity tests) with dt = 0.02 Myr x 10^U(-0.5, 0.5) per
+    step; each step samples per_step cells, half uniformly and half among the
+    cells the radiation reaches (Gamma_HI dt > 1e-4), and the oracle labels
+    them with its converged update in spawned worker processes.  configs:
+    (n, nsrc, seed) triples."""
+    import torch
+    import paper_1807_07094_gb300 as P
+    steps = []
+    pool = mp.get_context("spawn").Pool(workers)
+    pending = []
+    for (n, nsrc, seed) in configs:
+        w = W.cosmic(n=n, nsrc=nsrc, seed=seed)
+        p = w.params()
+        rng = np.random.Generator(np.random.PCG64(seed + seed0))
+        nH = np.asarray(w.nH, np.float32).reshape(-1)
+        with P.Arc(w.n, w.box_cm, p) as a:
+            a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
+            a.add_sources(w.src_pos, w.src_ndot)
+            for k in range(nsteps):
+                dt = float(DT0 * 10 ** rng.uniform(-0.5, 0.5))
+                g, h, _ = a.trace(dt, budget=True)          # budget=True waits for the rates
+                g = g.cpu().numpy().reshape(3, -1)
+                h = h.cpu().numpy().reshape(3, -1)
+                xs = [np.asarray(v, np.float32).reshape(-1) for v in a.get_fields()]
+                lit = np.flatnonzero(g[0] * dt > 1e-4)
+                half = per_step // 2
+                idx = rng.choice(nH.size, per_step - min(half, lit.size), replace=False)
+                if lit.size:
+                    idx = np.concatenate([idx, rng.choice(lit, min(half, lit.size), replace=False)])
+                idx = np.unique(idx)
+                st = dict(nH=nH[idx], x0=np.stack([xs[q][idx] for q in range(3)]), T0=xs[3][idx],
+                          gamma=np.ascontiguousarray(g[:, idx]), heat=np.ascontiguousarray(h[:, idx]), dt=dt)
+                chunks = np.array_split(np.arange(idx.size), max(1, idx.size // 2048))
+                pending.append((st, [pool.apply_async(_label_chunk, ((p, st["nH"][c], st["x0"][:, c], st["T0"][c],
+                                                                      st["gamma"][:, c], st["heat"][:, c], dt),))
+                                     for c in chunks]))
+                a.chem(dt)
+        print(f"  gpu states n={n} seed={seed}: {nsteps} steps", flush=True)
+    for st, res in pending:
+        out = [r.get() for r in res]
+        st["x1"] = np.concatenate([o[0] for o in out], axis=1)
+        st["T1"] = np.concatenate([o[1] for o in out])
+        steps.append(st)
+    pool.close()
+    pool.join()
+    return steps
+
+
+def evaluate(path_new, path_old=None, n=256, nsrc=1000, seed=1807, nsteps=3):
+    """Surrogate on a held-out state (the 256^3 benchmark field after nsteps):
+    accepted fraction with the new weights, the old ones and the predictor
+    alone (zero network output), and the accepted cells' distance from the
+    oracle's converged update on a seeded probe."""
+    import torch
+    import paper_1807_07094_gb300 as P
+    w = W.cosmic(n=n, nsrc=nsrc, seed=seed)
+    p = w.params()
+    res = {}
+    with P.Arc(w.n, w.box_cm, p) as a:
+        a.set_fields(w.nH, w.xHI, w.xHeI, w.xHeII, w.T)
+        a.add_sources(w.src_pos, w.src_ndot)
+        for _ in range(nsteps):
+            a.step(w.dt_s)
+        state = a.get_fields()
+        g, h, _ = a.trace(w.dt_s, budget=True)
+        g = g.cpu().numpy().reshape(3, -1)
+        h = h.cpu().numpy().reshape(3, -1)
+        n3 = w.n ** 3
+        rng = np.random.Generator(np.random.PCG64(99))
+        lit = np.flatnonzero(g[0] * w.dt_s > 1e-4)
+        probe = np.unique(np.concatenate([rng.choice(n3, 2048, replace=False), rng.choice(lit, 2048, replace=False)]))
+        f = lambda v: np.asarray(v, np.float32).reshape(-1)[probe]
+        xs, Ts = converged(p, f(w.nH).astype(np.float64), np.stack([f(state[q]) for q in range(3)]).astype(np.float64),
+                           f(state[3]).astype(np.float64), g[:, probe].astype(np.float64),
+                           h[:, probe].astype(np.float64), w.dt_s)
+        arms = {"new": P.load_surrogate(path_new)[:2]}
+        if path_old:
+            arms["old"] = P.load_surrogate(path_old)[:2]
+        pn, nn = arms["new"]
+        n0 = nn.copy()
+        n0[24:28] = 0.0
+        arms["predictor"] = (np.zeros_like(pn), n0)
+        for name, (prm, nrm) in arms.items():
+            a.set_fields(w.nH, *state)
+            a.set_surrogate(None)
+            a.chem(w.dt_s)
+            plain = [f(v) for v in a.get_fields()]
+            a.set_fields(w.nH, *state)
+            a.set_surrogate(prm, nrm)
+            a.chem(w.dt_s)
+            st = a.stats()
+            out = [f(v) for v in a.get_fields()]
+            a.set_surrogate(None)
+            acc = np.zeros(probe.size, bool)
+            for u, v in zip(plain, out):
+                acc |= u != v
+            dx = max(float(np.abs(out[q] - xs[q])[acc].max(initial=0.0)) for q in range(3))
+            dT = float(np.abs(out[3] / Ts - 1)[acc].max(initial=0.0))
+            res[name] = dict(accepted_frac=st["surrogate_cells"] / n3, chem_ms=st["chem_ms"],
+                             probe_accepted=int(acc.sum()), probe_max_dx=dx, probe_max_dT_rel=dT)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -111,23 +226,39 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--wd", type=float, default=1e-5)
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
+    ap.add_argument("--states", default="oracle", choices=["oracle", "gpu"],
+                    help="oracle: free-running oracle runs at --n; gpu: the C4 configurations (128^3 and "
+                         "256^3 cosmic fields) advanced on the GPU, cells labelled by the oracle")
+    ap.add_argument("--configs", default="128:125:201,128:125:202,128:125:203,128:125:204,256:1000:301,256:1000:302",
+                    help="n:nsrc:seed triples for --states gpu")
+    ap.add_argument("--evaluate-against", default="", help="old weights file to compare on the held-out state")
     a = ap.parse_args()
     seeds = [int(s) for s in a.seeds.split(",")]
     t0 = time.time()
-    steps = gather(seeds, a.n, a.nsrc, a.nsteps, a.per_step, a.workers)
+    if a.states == "gpu":
+        configs = [tuple(int(v) for v in c.split(":")) for c in a.configs.split(",")]
+        steps = gpu_states(configs, a.nsteps, a.per_step, a.workers)
+        seeds = [c[2] for c in configs]
+    else:
+        steps = gather(seeds, a.n, a.nsrc, a.nsteps, a.per_step, a.workers)
     t1 = time.time()
     print(f"oracle data: {len(steps)} steps in {t1 - t0:.0f} s", flush=True)
     from paper_1807_07094_gb300 import train as T
     P, norm, hist, nsamples = T.train_surrogate(steps, W.cosmic(n=8, nsrc=1).params(), a.epochs, a.batch,
                                                 a.lr, a.wd, seeds[0])
     t2 = time.time()
-    meta = dict(recipe="FP64 oracle trajectories of lognormal cosmic fields (sigma_ln 1.5, P(k)~k^-3, mean nH 2e-4); "
-                "labels: converged update (Richardson of sub-step caps dt/200, dt/400)",
+    recipe = ("FP64 oracle trajectories of lognormal cosmic fields (sigma_ln 1.5, P(k)~k^-3, mean nH 2e-4)"
+              if a.states == "oracle" else
+              "cosmic fields " + a.configs + " (n:nsrc:seed; sigma_ln 1.5, P(k)~k^-3, mean nH 2e-4) advanced on the "
+              "GPU, half of each step's cells sampled where Gamma_HI dt > 1e-4")
+    meta = dict(recipe=recipe + "; labels: the oracle's converged update (Richardson of sub-step caps dt/200, dt/400)",
                 n=a.n, nsrc=a.nsrc, nsteps=a.nsteps, seeds=seeds, per_step=a.per_step, samples=nsamples,
                 epochs=a.epochs,
                 batch=a.batch, lr=a.lr, wd=a.wd, loss=hist, oracle_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))
     T.save_weights(a.out, P, norm, meta)
     print(json.dumps(meta))
+    if a.evaluate_against is not None and a.states == "gpu":
+        print("EVAL " + json.dumps(evaluate(a.out, a.evaluate_against or None)), flush=True)
 
 
 if __name__ == "__main__":
