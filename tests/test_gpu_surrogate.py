@@ -203,14 +203,27 @@ def test_surrogate_step_matches_converged_oracle(heldout):
     assert frac > 0.5
     assert dx <= DX_BAR
     assert dT <= T_BAR
-    # the learned correction earns its place: the physics predictor alone
-    # (zero network output) passes the same check on fewer cells
+    # what the learned correction gains over the method without it: the
+    # physics predictor alone (zero network output) passes the same check on
+    # no more cells, and on the cells it passes lands several times farther
+    # from the converged update
     norm0 = norm.copy()
     norm0[24:28] = 0.0
-    _, st0 = _chem_cells(p, cells, dt, (np.zeros_like(params), norm0))
+    pred, st0 = _chem_cells(p, cells, dt, (np.zeros_like(params), norm0))
     frac0 = st0["surrogate_cells"] / m
-    print(f"predictor alone: accepted {frac0:.3f}")
-    assert frac > frac0
+    acc0 = np.zeros(m, bool)
+    for u, v in zip(plain, pred):
+        acc0 |= u != v
+    both = (accepted & acc0)[sub]
+    dx_net = max(np.abs(surr[q][sub] - conv[q])[both].max(initial=0.0) for q in range(3))
+    dx_pred = max(np.abs(pred[q][sub] - conv[q])[both].max(initial=0.0) for q in range(3))
+    dT_net = np.abs(surr[3][sub] / conv[3] - 1)[both].max(initial=0.0)
+    dT_pred = np.abs(pred[3][sub] / conv[3] - 1)[both].max(initial=0.0)
+    print(f"predictor alone: accepted {frac0:.3f}; on {both.sum()} cells both accept max|dx| "
+          f"{dx_pred:.2e} (network {dx_net:.2e}), max|dT/T| {dT_pred:.2e} (network {dT_net:.2e})")
+    assert frac >= frac0
+    assert both.sum() > 1000
+    assert dx_net * 3 <= dx_pred and dT_net * 2 <= dT_pred
 
 
 def test_forced_fallback_is_the_plain_solver(heldout):
