@@ -252,9 +252,11 @@ def main():
               "cosmic fields " + a.configs + " (n:nsrc:seed; sigma_ln 1.5, P(k)~k^-3, mean nH 2e-4) advanced on the "
               "GPU, half of each step's cells sampled where Gamma_HI dt > 1e-4")
     meta = dict(recipe=recipe + "; labels: the oracle's converged update (Richardson of sub-step caps dt/200, dt/400)",
-                n=a.n, nsrc=a.nsrc, nsteps=a.nsteps, seeds=seeds, per_step=a.per_step, samples=nsamples,
+                nsteps=a.nsteps, seeds=seeds, per_step=a.per_step, samples=nsamples,
                 epochs=a.epochs,
                 batch=a.batch, lr=a.lr, wd=a.wd, loss=hist, oracle_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))
+    if a.states == "oracle":
+        meta.update(n=a.n, nsrc=a.nsrc)
     T.save_weights(a.out, P, norm, meta)
     print(json.dumps(meta))
     if a.evaluate_against is not None and a.states == "gpu":
