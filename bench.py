@@ -136,14 +136,17 @@ def profiled_traffic():
         return None, None
     head = {}
     for ln in txt.splitlines():
-        for key in ("source_hash", "dram_bytes_per_segment", "l2_hit_rate"):
+        for key in ("source_hash", "dram_bytes_per_segment", "l2_hit_rate", "l2_atomic_alu_frac",
+                    "l2_atomic_input_max_slice_frac"):
             if ln.startswith(key + ":"):
                 head[key] = ln.split(":", 1)[1].strip()
     if head.get("source_hash") != kernel_source_hash():
         return None, head.get("source_hash")
     try:
-        return {"dram_bytes_per_segment": float(head["dram_bytes_per_segment"]),
-                "l2_hit_rate": float(head["l2_hit_rate"]) if "l2_hit_rate" in head else None}, head["source_hash"]
+        f = lambda k: float(head[k]) if k in head else None
+        return {"dram_bytes_per_segment": float(head["dram_bytes_per_segment"]), "l2_hit_rate": f("l2_hit_rate"),
+                "l2_atomic_alu_frac": f("l2_atomic_alu_frac"),
+                "l2_atomic_input_max_slice_frac": f("l2_atomic_input_max_slice_frac")}, head["source_hash"]
     except (KeyError, ValueError):
         return None, head.get("source_hash")
 
@@ -664,7 +667,11 @@ def run_ours(args):
                      "timing": "CUDA events around the trace inside each timed graph step",
                      # one returning 16-byte vector atomic per segment (L2)
                      "atomics_per_s": sum(trace_segs) / (sum(trace_ms) / 1e3),
-                     "l2_hit_rate": prof["l2_hit_rate"] if prof else None},
+                     "l2_hit_rate": prof["l2_hit_rate"] if prof else None,
+                     # the L2 atomic units' busy fraction against their sustained peak (ncu
+                     # capture of the same kernel): average over slices and the busiest slice
+                     "atomic_unit_frac": prof["l2_atomic_alu_frac"] if prof else None,
+                     "atomic_unit_frac_busiest_slice": prof["l2_atomic_input_max_slice_frac"] if prof else None},
         "e2e": {"value": tot_e2e / (max_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": 5 * 4 * n3,
                 "d2h_bytes_per_step": 4 * 4 * n3},
         "surrogate": surrogate,
