@@ -9,6 +9,15 @@ resident in HBM; every input array is larger than L2).  ``e2e`` repeats the
 measurement through the C ABI with host buffers: the gas state is copied in
 from pinned host memory and the new state copied out in every step.
 
+After the timed steps the line also carries: the error against the FP64 oracle
+of a seeded sample of the sources traced alone on the final gas state
+(``oracle_error``: rates per cell, ray trees, absorbed photons); the oracle's
+own speed on the host cores (``cpu_baseline``, the CPU leg, which alone runs
+the oracle); and the learned chemistry surrogate against the plain solver at
+equal accuracy, both judged against the oracle's converged update
+(``surrogate``).  ``--workload cosmic_512`` runs the 512^3 x 10^4-source
+configuration instead.
+
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload (the paper publishes no code; the oracle is the reference).
 For N > 1 the step runs as N independent replicas, one per rank (sharding the
