@@ -244,6 +244,17 @@ def _oracle_source_job(args):
     return k, int(r["nseg"]), cpu
 
 
+def _oracle_chem_job(args):
+    """The paper's sub-cycled update of one slice of cells (a spawned worker of
+    the CPU leg)."""
+    params, nH, x0, T0, g, h, dt = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    t0 = time.perf_counter()
+    oracle.chem(params, nH, x0[0], x0[1], x0[2], T0, g, h, dt)
+    return time.perf_counter() - t0
+
+
 def cpu_leg(w, state, sample, gpu_sample, gpu_tree, chem_probe, max_workers: int = 0):
     """The FP64 oracle on the host cores (a reported baseline), on the same
     bounded sample the GPU traced after the timed steps, and the GPU's error
@@ -348,6 +359,18 @@ def cpu_leg(w, state, sample, gpu_sample, gpu_tree, chem_probe, max_workers: int
         ncell = len(cp["nH"])
         base["chem_cells_per_s"] = ncell / tc
         base["chem_sample"] = f"paper's sub-cycled update of {ncell} probe cells, one core"
+        if "bulk" in cp:
+            bk = cp["bulk"]
+            m = bk["nH"].size
+            parts = np.array_split(np.arange(m), ncores)
+            jobs = [(p, bk["nH"][q], [bk["x0"][k][q] for k in range(3)], bk["T0"][q], bk["gamma"][:, q],
+                     bk["heat"][:, q], cp["dt"]) for q in parts]
+            with mp.get_context("spawn").Pool(ncores) as pool:
+                took = pool.map(_oracle_chem_job, jobs)
+            wall = max(took)
+            base["chem_cells_per_s_all_cores"] = m / wall
+            base["chem_sample"] += (f"; {m} uniformly drawn cells of the same state on {ncores} cores, one "
+                                    f"slice per spawned process: {wall:.3f} s for the slowest slice")
 
         def err(out, ref):
             dx = max(float(np.max(np.abs(out[i] - ref[i]))) for i in range(3))
@@ -464,6 +487,11 @@ def surrogate_speedup(a, w, P, stream, reps: int = 3, probe_random: int = 2048, 
     probe = {"nH": flat(w.nH), "x0": [flat(state[k]) for k in range(3)], "T0": flat(state[3]),
              "gamma": gamma[:, cells].astype(np.float64), "heat": heat[:, cells].astype(np.float64),
              "dt": w.dt_s, "arms": {k: [flat(v["out"][q]) for q in range(4)] for k, v in arms.items()}}
+    # a uniform sample of cells for timing the oracle's chemistry on the host cores
+    bulk = np.sort(rng.choice(n3, size=min(1 << 18, n3), replace=False))
+    fb = lambda a_: np.asarray(a_, np.float32).reshape(-1)[bulk].astype(np.float64)
+    probe["bulk"] = {"nH": fb(w.nH), "x0": [fb(state[k]) for k in range(3)], "T0": fb(state[3]),
+                     "gamma": gamma[:, bulk].astype(np.float64), "heat": heat[:, bulk].astype(np.float64)}
     rec = lambda r, eps: {"eps": eps, "ms": r["ms"], "cells_per_s": n3 / (r["med"] / 1e3),
                           "substeps_per_cell": r["stats"]["chem_substeps"] / n3}
     out = {"plain_paper_eps": rec(paper, w.params()["eps_sub"]),
