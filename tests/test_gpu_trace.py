@@ -103,7 +103,7 @@ def test_fp64_source_positions_as_given():
     the same values through arc_add_sources, which keeps them as FP32 pairs.
     Trees and rates must match at the usual bars; a plain FP32 position (off by
     up to ~4e-6 cell here) moves photons behind thick cells by more than 1e-4."""
-    w = W.cosmic(n=48, nsrc=8, sigma_ln=1.5, seed=21, quantise=False)
+    w = W.cosmic(n=48, nsrc=8, sigma_ln=1.5, seed=21)
     assert np.any(np.abs(w.src_pos - W.quantise_pos(w.src_pos)) > 1e-6)
     assert np.any(w.src_pos.astype(np.float32).astype(np.float64) != w.src_pos)
     xs = partly_ionised(w, seed=22, lo=-4, hi=0)

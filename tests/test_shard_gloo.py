@@ -80,5 +80,7 @@ def test_sharded_trace_sums_to_the_unsharded_one(tmp_path, world):
             assert np.max(np.abs(r[name][m] - ref[m]) / ref[m]) < 1e-12
         em, ab, es = r["budget"]
         assert abs(em / full["budget"][0] - 1) < 1e-14
-        assert abs(ab / full["budget"][1] - 1) < 1e-12
+        # the absorbed photons are a long FP64 running sum per trace (one
+        # addition per segment); summing per-rank totals reorders it
+        assert abs(ab / full["budget"][1] - 1) < 1e-10
         assert abs(em - ab - es) <= 1e-9 * em

@@ -1,5 +1,5 @@
 """Host checks of the seeded input generators (no method arithmetic lives
-here): positions exact in FP32, the ionised-sphere state against a brute-force
+here): source positions as drawn or on the FP32 grid, the ionised-sphere state against a brute-force
 distance test, and reproducibility from the seed."""
 import numpy as np
 import pytest
@@ -7,10 +7,15 @@ import pytest
 import workloads as W
 
 
-def test_positions_are_exact_in_fp32():
+def test_positions_as_drawn_or_on_the_fp32_grid():
+    """By default source positions are the FP64 draws (the tracer carries them as
+    FP32 pairs); quantise=True rounds them to 2^-12 cell, exact in FP32."""
     w = W.cosmic(n=32, nsrc=20, seed=3)
-    assert np.array_equal(w.src_pos.astype(np.float32).astype(np.float64), w.src_pos)
+    q = W.cosmic(n=32, nsrc=20, seed=3, quantise=True)
     assert ((w.src_pos >= 0) & (w.src_pos < w.n)).all()
+    assert not np.array_equal(w.src_pos.astype(np.float32).astype(np.float64), w.src_pos)
+    assert np.array_equal(q.src_pos.astype(np.float32).astype(np.float64), q.src_pos)
+    assert np.abs(q.src_pos - w.src_pos).max() <= 2.0 ** -13
 
 
 def test_cosmic_field_is_seeded():

@@ -233,10 +233,10 @@ def cosmic_field(n: int, sigma_ln: float, mean_nH: float, seed: int) -> np.ndarr
 
 
 def place_sources(nH: np.ndarray, nsrc: int, ndot_lo: float, ndot_hi: float,
-                  frac: np.ndarray, seed: int, quantise: bool = True):
+                  frac: np.ndarray, seed: int, quantise: bool = False):
     """Sources in cells drawn ~ nH^2 (with replacement), jittered by U(-0.4,0.4)
-    cells, positions quantised to 2^-12 (or left as drawn, FP64, with
-    quantise=False); luminosities log-uniform."""
+    cells, positions as drawn (FP64; quantise=True rounds them to 2^-12 cell);
+    luminosities log-uniform."""
     rng = np.random.Generator(np.random.PCG64(seed + 7919))
     w = nH.astype(np.float64).ravel() ** 2
     w /= w.sum()
@@ -252,7 +252,7 @@ def place_sources(nH: np.ndarray, nsrc: int, ndot_lo: float, ndot_hi: float,
 
 def cosmic(n: int = 256, nsrc: int = 1000, sigma_ln: float = 1.5, seed: int = 1807,
            ndot_lo: float = 1e48, ndot_hi: float = 1e51, box_kpc: Optional[float] = None,
-           mean_nH: float = 2e-4, quantise: bool = True) -> Workload:
+           mean_nH: float = 2e-4, quantise: bool = False) -> Workload:
     """Lognormal cosmic-field workload (stand-in for RT06 Test 4)."""
     grp = blackbody_groups(1e5)
     nH = cosmic_field(n, sigma_ln, mean_nH, seed)
