@@ -98,6 +98,14 @@ __device__ __forceinline__ float two_sum_err(float a, float b) {
     return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// rounding error of a + b for a, b >= 0: Fast2Sum on the larger and the
+// smaller operand (exact, and the same value TwoSum gives, in five operations
+// instead of six)
+__device__ __forceinline__ float add_err_nonneg(float a, float b) {
+    const float hi = fmaxf(a, b), lo = fminf(a, b);
+    const float s = __fadd_rn(hi, lo);
+    return __fsub_rn(lo, __fsub_rn(s, hi));
+}
 // Eq. (ion) for one group: the fraction a = 1 - exp(-tau) of the ray's
 // photons is absorbed.  The ray carries its photons as an unevaluated pair
 // Nh + Nl, so that it can lose exactly what the cell receives without the
@@ -136,9 +144,8 @@ __device__ __forceinline__ void absorb(float& Nh, float& Nl, float tau, float& d
         const float a = thin_fraction(tau);
         d = __fmul_rn(Nh, a);
         e = 0.0f;
-        const float s = __fsub_rn(Nh, d);                 // TwoSum(Nh, -d) = (s, r)
-        const float bb = __fsub_rn(s, Nh);
-        const float r = __fadd_rn(__fsub_rn(Nh, __fsub_rn(s, bb)), __fsub_rn(-d, bb));
+        const float s = __fsub_rn(Nh, d);                 // Fast2Sum(Nh, -d) = (s, r): d <= Nh / 2
+        const float r = __fsub_rn(__fsub_rn(Nh, s), d);
         const float lo = __fadd_rn(Nl, r);
         Nh = __fadd_rn(s, lo);                            // renormalise (|lo| << |s|)
         Nl = __fsub_rn(lo, __fsub_rn(Nh, s));
@@ -147,9 +154,8 @@ __device__ __forceinline__ void absorb(float& Nh, float& Nl, float tau, float& d
         // (argument rounding), and through thick gas it would accumulate along
         // the ray
         const float Nn = __fmul_rn(Nh, expf(-tau));
-        d = __fsub_rn(Nh, Nn);                            // TwoSum(Nh, -Nn) = (d, r)
-        const float bb = __fsub_rn(d, Nh);
-        const float r = __fadd_rn(__fsub_rn(Nh, __fsub_rn(d, bb)), __fsub_rn(-Nn, bb));
+        d = __fsub_rn(Nh, Nn);                            // Fast2Sum(Nh, -Nn) = (d, r): Nn <= Nh / 2
+        const float r = __fsub_rn(__fsub_rn(Nh, d), Nn);
         e = __fadd_rn(r, Nl);
         Nh = Nn;
         Nl = 0.0f;
@@ -165,17 +171,18 @@ __device__ __forceinline__ void fold_low(float& Nh, float& Nl, float lo) {
 
 // Vector deposit of D = d + e into a cell's FP32 accumulator: the atomic
 // returns the old value, from which the rounding error of old + d is
-// recovered exactly (TwoSum); that error plus e, the part of the deposit below
+// recovered exactly (both are >= 0: Fast2Sum on the larger of the two); that
+// error plus e, the part of the deposit below
 // d's precision, is returned for the caller's rounding ledger.  The cell sums
 // are then plain FP32 (relative error ~1e-7, far below the rates' needs) while
 // the photon budget, cells plus ledger plus escapes, stays exact.
 template <int NG>
 __device__ __forceinline__ float deposit(float4* rec, uint64_t idx, float4 d, float4 e) {
     const float4 old = atom_add_v4(rec + 2 * idx + 1, d);
-    float err = __fadd_rn(two_sum_err(old.x, d.x), e.x);
-    if (NG > 1) err = __fadd_rn(err, __fadd_rn(two_sum_err(old.y, d.y), e.y));
-    if (NG > 2) err = __fadd_rn(err, __fadd_rn(two_sum_err(old.z, d.z), e.z));
-    if (NG > 3) err = __fadd_rn(err, __fadd_rn(two_sum_err(old.w, d.w), e.w));
+    float err = __fadd_rn(add_err_nonneg(old.x, d.x), e.x);
+    if (NG > 1) err = __fadd_rn(err, __fadd_rn(add_err_nonneg(old.y, d.y), e.y));
+    if (NG > 2) err = __fadd_rn(err, __fadd_rn(add_err_nonneg(old.z, d.z), e.z));
+    if (NG > 3) err = __fadd_rn(err, __fadd_rn(add_err_nonneg(old.w, d.w), e.w));
     return err;
 }
 
