@@ -211,6 +211,14 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
     const float e = __fadd_rn(two_sum_err(a.h, b.h), __fadd_rn(a.l, b.l));
     return fast_two_sum(s, e);
 }
+// a + b for a.h, b.h >= 0: the rounding error of the high parts by Fast2Sum
+// on the larger of the two (the same value as f2_add's TwoSum)
+__device__ __forceinline__ F2 f2_add_pos(F2 a, F2 b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float hi = fmaxf(a.h, b.h), lo = fminf(a.h, b.h);
+    const float e = __fadd_rn(__fsub_rn(lo, __fsub_rn(s, hi)), __fadd_rn(a.l, b.l));
+    return fast_two_sum(s, e);
+}
 __device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
     const float p = __fmul_rn(a.h, b.h);
     const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
@@ -651,7 +659,7 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
         const float ih = ax ? R.ix : (ay ? R.iy : R.iz);
         const float il = ax ? R.ilx : (ay ? R.ily : R.ilz);
         const bool up = ih > 0.0f;
-        const F2 tn = f2_add(F2{t, tl}, F2{fabsf(ih), up ? il : -il});
+        const F2 tn = f2_add_pos(F2{t, tl}, F2{fabsf(ih), up ? il : -il});
         const int c = (ax ? R.cx : (ay ? R.cy : R.cz)) + (up ? 1 : -1);
         const uint32_t mk = ax ? 0x124u : (ay ? 0x92u : 0x49u);
         const uint32_t bs = ax ? A.bstride_x : (ay ? A.bstride_y : 512u);
@@ -687,9 +695,9 @@ __device__ __forceinline__ int segment(const TraceArgs& A, Ray& R, float& rerr) 
         D.w = __fsub_rn(D.w, Dn.w);
         rerr = __fadd_rn(rerr, deposit<NG>(A.acc, nidx, Dn, make_float4(0.f, 0.f, 0.f, 0.f)));
     }
-    if (D.x != 0.f || D.y != 0.f || D.z != 0.f || D.w != 0.f || E.x != 0.f || E.y != 0.f ||
-        E.z != 0.f || E.w != 0.f)
-        rerr = __fadd_rn(rerr, deposit<NG>(A.acc, idx, D, E));
+    // unconditional: a segment that deposits nothing (an empty cell) adds zeros,
+    // which leaves the cell and the ledger as they were
+    rerr = __fadd_rn(rerr, deposit<NG>(A.acc, idx, D, E));
     return ev;
 }
 
