@@ -146,7 +146,7 @@ def profiled_traffic():
     head = {}
     for ln in txt.splitlines():
         for key in ("source_hash", "dram_bytes_per_segment", "l2_hit_rate", "l2_atomic_alu_frac",
-                    "l2_atomic_input_max_slice_frac"):
+                    "l2_atomic_input_max_slice_frac", "traffic_case", "l2_case"):
             if ln.startswith(key + ":"):
                 head[key] = ln.split(":", 1)[1].strip()
     if head.get("source_hash") != kernel_source_hash():
@@ -154,7 +154,8 @@ def profiled_traffic():
     try:
         f = lambda k: float(head[k]) if k in head else None
         return {"dram_bytes_per_segment": float(head["dram_bytes_per_segment"]), "l2_hit_rate": f("l2_hit_rate"),
-                "l2_atomic_alu_frac": f("l2_atomic_alu_frac"),
+                "l2_atomic_alu_frac": f("l2_atomic_alu_frac"), "traffic_case": head.get("traffic_case"),
+                "l2_case": head.get("l2_case"),
                 "l2_atomic_input_max_slice_frac": f("l2_atomic_input_max_slice_frac")}, head["source_hash"]
     except (KeyError, ValueError):
         return None, head.get("source_hash")
@@ -699,6 +700,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": (traffic_per_seg * sum(trace_segs) / len(trace_segs)) if traffic_per_seg else None,
+                     # the DRAM bytes those counters give per segment, moved in the measured time
+                     "dram_achieved": (traffic_per_seg * sum(trace_segs) / (sum(trace_ms) / 1e3) / 1e9)
+                     if traffic_per_seg else None,
+                     "dram_frac": (traffic_per_seg * sum(trace_segs) / (sum(trace_ms) / 1e3) / 1e9 / hbm)
+                     if traffic_per_seg else None,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if pk else "fallback 6.8 TB/s",
                      "kernel": "k_trace", "algo_bytes_per_segment": ALGO_BYTES_PER_SEGMENT,
                      "timing": "CUDA events around the trace inside each timed graph step",
@@ -708,7 +714,8 @@ def run_ours(args):
                      # the L2 atomic units' busy fraction against their sustained peak (ncu
                      # capture of the same kernel): average over slices and the busiest slice
                      "atomic_unit_frac": prof["l2_atomic_alu_frac"] if prof else None,
-                     "atomic_unit_frac_busiest_slice": prof["l2_atomic_input_max_slice_frac"] if prof else None},
+                     "atomic_unit_frac_busiest_slice": prof["l2_atomic_input_max_slice_frac"] if prof else None,
+                     "profile_cases": {"traffic": prof["traffic_case"], "l2": prof["l2_case"]} if prof else None},
         "e2e": {"value": tot_e2e / (max_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": 5 * 4 * n3,
                 "d2h_bytes_per_step": 4 * 4 * n3},
         "surrogate": surrogate,
