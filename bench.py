@@ -15,7 +15,12 @@ of a seeded sample of the sources traced alone on the final gas state
 own speed on the host cores (``cpu_baseline``, the CPU leg, which alone runs
 the oracle); and the learned chemistry surrogate against the plain solver at
 equal accuracy, both judged against the oracle's converged update
-(``surrogate``).  ``--workload cosmic_512`` runs the 512^3 x 10^4-source
+(``surrogate``).  ``roofline`` gives k_trace's algorithmic bytes per second
+against the measured HBM copy bandwidth and, from the committed ncu summary
+while its source hash matches the tracer, the DRAM bytes those counters give
+per segment (``traffic``, ``dram_achieved``, ``dram_frac``), the L2 hit rate
+and the L2 atomic units' busy fractions, naming the capture each comes from
+(``profile_cases``).  ``--workload cosmic_512`` runs the 512^3 x 10^4-source
 configuration instead.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
